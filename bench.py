@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: hierarchization of combination grids on one GB300 (per rank).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--forms]
+
+Headline workload (one step): hierarchize + dehierarchize (round trip) of the
+3-D fp64 grid of level (9,9,9) -- 513^3 = 135,005,697 points, 1.08 GB -- with
+values sin(2 pi x) exp(-y) (1 + z^2) + 1e-3 N(0,1) (seed 1).  The grid is
+larger than L2, so no flush is needed between steps.  value = grid points
+transformed per second (each of the two transforms counts N points), whole
+job (all ranks).  With N > 1 every rank transforms its own grid: the
+single-grid path does not shard (replicas, weak scaling).
+
+`--forms` adds the other forms of the method measured in the same run:
+plain per-dimension path, adjoint, fp32 5-D grid, batched combination scheme
+with the sparse-grid gather, differentiation batch.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gpoints/s & HBM GB/s (% roofline): fwd/adjoint, batched+FP32 vs plain FP64"
+UNIT = "Gpoints/s"
+WORKLOAD = "hierarchize+dehierarchize round trip, d=3 level (9,9,9) fp64 single grid (513^3 points, 1.08 GB)"
+LEVELS2 = (9, 9, 9)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    smax.append(float(parts[2].split()[0]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands
+# ---------------------------------------------------------------------------
+
+def cpu_round_trip(levels, u, reps):
+    import oracle
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        a = oracle.hierarchize(u, levels)
+        u = oracle.dehierarchize(a, levels)
+    dt = time.perf_counter() - t0
+    return 2.0 * u.size * reps / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1309_0392_gb300 import inputs
+    levels = (9, 9, 6)                   # bounded sample: 513 x 513 x 65 slab of the grid's shape
+    u = inputs.cfg2(levels)[1]
+    for _ in range(args.warmup):
+        cpu_round_trip(levels, u, 1)
+    v, dt = cpu_round_trip(levels, u, args.steps)
+    sample = (f"oracle round trip on a (9,9,6) grid (513x513x65 = {u.size} points) per step, "
+              "same value recipe; serial C, 1 thread")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def time_region(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def dominant_kernel(prof):
+    """(name, launches, avg_ms, alg_bytes_per_launch) of the kernel with the
+    largest total device time."""
+    if not prof:
+        return None
+    name, (n, ms, by) = max(prof.items(), key=lambda kv: kv[1][1])
+    return name, n, ms / n, by / n
+
+
+def forms(args, dev, hbm):
+    """Secondary measurements: each form of the method on its own workload."""
+    import torch
+
+    import paper_1309_0392_gb300 as gbh
+    from paper_1309_0392_gb300 import inputs
+    out = {}
+    st = torch.cuda.current_stream()
+
+    def measure(name, t, levels, op, reps, es, path=gbh.GBH_PATH_AUTO, batch=None, restore=None):
+        for _ in range(2):
+            gbh.transform(t, levels, op, path=path, batch=batch)
+            if restore is not None:
+                restore()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            gbh.transform(t, levels, op, path=path, batch=batch)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            if restore is not None:
+                restore()
+        ms = float(np.median(times))
+        pts = t.numel()
+        gbs = 2.0 * es * pts / (ms * 1e-3) / 1e9
+        out[name] = {"Gpts_s": pts / (ms * 1e-3) / 1e9, "GB_s": gbs, "frac_of_hbm": gbs / hbm, "ms": ms,
+                     "points": pts}
+
+    # plain per-dimension path and adjoint on the headline grid
+    _, u2 = inputs.cfg2()
+    t = torch.tensor(u2, device=dev)
+    measure("fwd_plain_fp64_9_9_9", t, LEVELS2, gbh.GBH_HIERARCHIZE, 5, 8, path=gbh.GBH_PATH_PLAIN,
+            restore=lambda: gbh.transform(t, LEVELS2, gbh.GBH_DEHIERARCHIZE, path=gbh.GBH_PATH_PLAIN))
+    measure("fwd_fp64_9_9_9", t, LEVELS2, gbh.GBH_HIERARCHIZE, 5, 8,
+            restore=lambda: gbh.transform(t, LEVELS2, gbh.GBH_DEHIERARCHIZE))
+    measure("dehier_fp64_9_9_9", t, LEVELS2, gbh.GBH_DEHIERARCHIZE, 5, 8,
+            restore=lambda: gbh.transform(t, LEVELS2, gbh.GBH_HIERARCHIZE))
+    t.copy_(torch.from_numpy(np.random.default_rng(3).uniform(-1, 1, t.numel())))
+    measure("adjoint_fp64_9_9_9", t, LEVELS2, gbh.GBH_ADJOINT, 5, 8)
+    del t
+    # fp32 5-D grid
+    lv3, u3 = inputs.cfg3()
+    t = torch.tensor(u3.astype(np.float32), device=dev)
+    measure("fwd_fp32_6_6_5_5_5", t, lv3, gbh.GBH_HIERARCHIZE, 5, 4,
+            restore=lambda: gbh.transform(t, lv3, gbh.GBH_DEHIERARCHIZE))
+    measure("fwd_plain_fp32_6_6_5_5_5", t, lv3, gbh.GBH_HIERARCHIZE, 5, 4, path=gbh.GBH_PATH_PLAIN,
+            restore=lambda: gbh.transform(t, lv3, gbh.GBH_DEHIERARCHIZE, path=gbh.GBH_PATH_PLAIN))
+    del t
+    # differentiation batch: adjoint of 16 grids of level (8,8,8)
+    lv5, u5 = inputs.cfg5()
+    for dt, es, nm in ((torch.float64, 8, "fp64"), (torch.float32, 4, "fp32")):
+        t = torch.tensor(u5.reshape(-1), dtype=dt, device=dev)
+        measure(f"adjoint_{nm}_16x_8_8_8", t, lv5, gbh.GBH_ADJOINT, 5, es, batch=16)
+        measure(f"fwd_{nm}_16x_8_8_8", t, lv5, gbh.GBH_HIERARCHIZE, 5, es, batch=16)
+        del t
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1309_0392_gb300 as gbh
+    from paper_1309_0392_gb300 import _lib, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    _lib.lib()
+    hbm, peak_kind = peaks()
+
+    levels, u = inputs.cfg2()
+    N = u.size
+    host = torch.from_numpy(u).pin_memory()
+    grid = host.to(dev, non_blocking=False)
+    st = torch.cuda.current_stream()
+
+    def step():
+        gbh.hierarchize(grid, levels)
+        gbh.dehierarchize(grid, levels)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    n0 = _lib.launch_count()
+    barrier()
+    ms = time_region(step, args.steps, st)
+    barrier()
+    launches = _lib.launch_count() - n0
+    _lib.profile_enable(False)
+    prof = _lib.profile_read()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    value = 2.0 * N * world / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    out_host = torch.empty_like(host).pin_memory()
+
+    def e2e_step():
+        grid.copy_(host, non_blocking=True)
+        gbh.hierarchize(grid, levels)
+        gbh.dehierarchize(grid, levels)
+        out_host.copy_(grid, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = time_region(e2e_step, max(2, args.steps // 2), st) / max(2, args.steps // 2)
+    barrier()
+    e2e_val = 2.0 * N * world / (ms_e2e * 1e-3) / 1e9
+
+    dom = dominant_kernel(prof)
+    roof = None
+    if dom is not None:
+        name, n, avg_ms, by = dom
+        achieved = by / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": f"{peak_kind} (burst copy)", "traffic": None,
+                "alg_bytes_per_launch": by, "avg_launch_ms": avg_ms, "launches": n}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": list(levels), "points": N, "grids_per_rank": 1,
+                       "l2": "inputs larger than L2 (1.08 GB grid), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_GB_s": value * 16.0, "frac_of_hbm": value * 16.0 / world / hbm,
+            "gpu_launches": launches,
+            "kernels": {k: {"launches": v[0], "ms": v[1], "alg_GB_s": v[2] / (v[1] * 1e-3) / 1e9 if v[1] else None}
+                        for k, v in prof.items()},
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+            "clocks": clk}
+    del grid
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if args.forms:
+            line["forms"] = forms(args, dev, hbm)
+        if not args.no_cpu:
+            reps = 3
+            v, dt = cpu_round_trip(levels, u, reps)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{reps} oracle round trips of the full (9,9,9) grid "
+                                              f"({dt:.1f} s, serial C, 1 thread of {os.cpu_count()})"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * gbh.h -- C ABI of the GB300 (sm_103a) hierarchization library, libgbh.so.
+ *
+ * The library changes the basis of anisotropic full "combination grids" of the
+ * sparse grid combination technique between the nodal basis and the
+ * piecewise-linear hierarchical basis (P. Hupp, "Hierarchization for the
+ * Sparse Grid Combination Technique", arXiv 1309.0392, Sec. 2-3).
+ *
+ * Grid layout (all entry points).  A grid of level vector l[0..d-1] has
+ * n_k = 2^{l_k} + 1 points in dimension k, boundary included, and is stored
+ * densely in "standard row major order" (Sec. 3) with dimension 0 contiguous:
+ * element (i_0, ..., i_{d-1}) sits at offset i_0 + n_0 (i_1 + n_1 (i_2 + ...)).
+ * levels[0] therefore belongs to the contiguous dimension.  The paper numbers
+ * dimensions 1..d with x_1 fastest; this is the same order, 0-based.
+ *
+ * Memory and ownership.  Every pointer to grid data is a DEVICE pointer owned
+ * by the caller; transforms work in place.  `levels` and other small arrays
+ * are HOST pointers read during the call only.  Element alignment (4 bytes for
+ * GBH_F32, 8 for GBH_F64) is required; nothing else.  The single-grid entry
+ * points allocate no device memory.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Calls are stream-ordered and asynchronous: the return code
+ * reports argument errors and launch errors; kernels may still be running when
+ * the call returns.
+ *
+ * Errors.  Every entry point returns a gbh_status (0 = success).  On an
+ * argument error nothing is launched and the data is untouched.
+ */
+#ifndef GBH_H
+#define GBH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { GBH_F32 = 0, GBH_F64 = 1 } gbh_dtype;
+
+typedef enum {
+    GBH_OK = 0,
+    GBH_EINVAL = -1,    /* null pointer, d out of [1, 16], bad op/path value   */
+    GBH_EDTYPE = -2,    /* dtype not GBH_F32 / GBH_F64                          */
+    GBH_EALIGN = -3,    /* data pointer not aligned to the element size         */
+    GBH_ERANGE = -4,    /* a level outside [0, 30], or the point count or the
+                           byte size overflows int64                            */
+    GBH_ECUDA = -5,     /* a CUDA call or kernel launch failed                  */
+    GBH_ETIMEOUT = -6,  /* a bounded device-side wait expired (batched plans)   */
+    GBH_ENOMEM = -7,    /* host or device allocation failed (plans only)        */
+    GBH_EUNSUPPORTED = -8 /* option not available for this shape or dtype       */
+} gbh_status;
+
+/* Transform selector. */
+typedef enum {
+    GBH_HIERARCHIZE = 0,    /* nodal -> hierarchical (Alg. 1)                    */
+    GBH_DEHIERARCHIZE = 1,  /* hierarchical -> nodal (inverse of Alg. 1)         */
+    GBH_ADJOINT = 2         /* transpose of Alg. 1                               */
+} gbh_op;
+
+/* ------------------------------------------------------------------------ */
+/* Single grid (the paper's problem statement: "a d dimensional combination  */
+/* grid of level vector (l_1, ..., l_d)", Sec. 3, Flop Count)                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Hierarchize in place: Alg. 1 (Sec. 3) in its boundary form.  For every
+ * dimension and every 1-D pole along it, every interior point i of level j
+ * becomes u[i] - 0.5 * (u[i - s] + u[i + s]), s = 2^{l_k - j}, computed from
+ * the nodal values; boundary points are unchanged.
+ *   data   : device pointer to N = prod_k (2^{l_k}+1) elements of `dtype`
+ *   d      : number of dimensions, 1..16
+ *   levels : host array of d levels, each 0..30 (level 0 = two points)
+ *   dtype  : GBH_F32 or GBH_F64
+ *   stream : cudaStream_t as void*
+ */
+int gbh_hierarchize(void *data, int d, const int32_t *levels, int dtype, void *stream);
+
+/*
+ * Dehierarchize in place: the exact inverse of gbh_hierarchize (the
+ * hierarchical-to-nodal step of the iterated combination technique, Sec. 2).
+ * Per pole, coarse to fine: u[i] = alpha[i] + 0.5 * (u[i - s] + u[i + s]).
+ * Arguments as for gbh_hierarchize.
+ */
+int gbh_dehierarchize(void *data, int d, const int32_t *levels, int dtype, void *stream);
+
+/*
+ * Adjoint in place: the exact transpose of gbh_hierarchize.  Per pole, every
+ * point p collects y[p] = x[p] - 0.5 * (sum of x over the points whose
+ * hierarchical predecessor p is).  Arguments as for gbh_hierarchize.
+ */
+int gbh_hierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype, void *stream);
+
+/* Execution path of gbh_transform. */
+typedef enum {
+    GBH_PATH_AUTO = 0,   /* planner's choice (fused when available)             */
+    GBH_PATH_PLAIN = 1,  /* one sweep kernel per dimension, native arithmetic   */
+    GBH_PATH_FUSED = 2   /* dyadic-tile kernels, all dimensions per tile        */
+} gbh_path;
+
+/* Options of gbh_transform.  Zero-initialise, then set what is wanted. */
+typedef struct {
+    int32_t path;          /* gbh_path                                          */
+    int32_t tile_exp[16];  /* fused path: tile exponent m_k per dimension
+                              (tile edge 2^{m_k}+1, 0 <= m_k <= l_k); all 0 =
+                              the planner chooses                               */
+    int32_t arith;         /* fused path, GBH_F64: 0 = planner's choice,
+                              1 = native fp64, 2 = int64 block fixed point       */
+    int32_t reserved[6];
+} gbh_options;
+
+/*
+ * General form of the three single-grid calls with an explicit op and
+ * execution options (NULL = defaults).  Used by tests and the tuner to pin a
+ * path; the results of every path agree with the oracle within the stated
+ * tolerance.
+ */
+int gbh_transform(void *data, int d, const int32_t *levels, int dtype, int op,
+                  const gbh_options *opt, void *stream);
+
+/*
+ * Same-shape batch: `batch` grids of one level vector stored back to back
+ * (grid b starts at element b * N), each transformed as by gbh_transform.
+ * batch >= 1; the other arguments as for gbh_transform.  Used for the
+ * differentiation workload (a batch of equal grids).
+ */
+int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *levels, int dtype,
+                          int op, const gbh_options *opt, void *stream);
+
+/*
+ * Number of grid points prod_k (2^{l_k}+1) into *out.  Host only.
+ */
+int gbh_num_points(int d, const int32_t *levels, int64_t *out);
+
+/* ------------------------------------------------------------------------ */
+/* Combination scheme (Sec. 2): batched transform and sparse-grid gather     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct gbh_plan gbh_plan;
+
+/*
+ * Plan for the regular combination scheme of dimension d and level n: every
+ * level vector with l_k >= 1 and |l|_1 = n + d - 1 - q, q = 0..d-1, with
+ * coefficient (-1)^q C(d-1, q) (Sec. 2, "The Combination Technique").  Grids
+ * are enumerated q ascending, then lexicographically (l_0 most significant).
+ * The plan owns its device work tables (allocated here; freed by
+ * gbh_plan_destroy) but not the grids.
+ *   d in [1, 8], n >= 1, dtype GBH_F32 or GBH_F64.  *out receives the plan.
+ */
+int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out);
+
+/*
+ * Plan for an arbitrary list of grids: levels is a host array [n_grids][d].
+ * Coefficients are 1 unless set with gbh_plan_set_coeffs; gbh_plan_gather
+ * needs a plan made by gbh_plan_create_scheme.
+ */
+int gbh_plan_create(int n_grids, int d, const int32_t *levels, int dtype, gbh_plan **out);
+
+int gbh_plan_destroy(gbh_plan *plan);
+
+/* Number of grids; level vector of grid g (d values) into levels_out. */
+int gbh_plan_num_grids(const gbh_plan *plan, int *out);
+int gbh_plan_grid_levels(const gbh_plan *plan, int g, int32_t *levels_out);
+/* Combination coefficients of all grids (n_grids doubles) into coeffs_out. */
+int gbh_plan_coeffs(const gbh_plan *plan, double *coeffs_out);
+/* Points of the sparse grid (scheme plans), total grid points (all plans). */
+int gbh_plan_sparse_points(const gbh_plan *plan, int64_t *out);
+int gbh_plan_total_points(const gbh_plan *plan, int64_t *out);
+
+/*
+ * Bind the device pointers of the grids: host array of n_grids device
+ * pointers, grid g holding gbh_num_points(levels of g) elements.  The table is
+ * copied to the device on `stream`; later executions use it until the next
+ * bind.  Must be called before gbh_plan_execute.
+ */
+int gbh_plan_bind(gbh_plan *plan, void *const *grid_ptrs, void *stream);
+
+/*
+ * Transform every bound grid in place (op = gbh_op) with one persistent
+ * kernel launch driven by a device work queue.
+ */
+int gbh_plan_execute(gbh_plan *plan, int op, void *stream);
+
+/*
+ * Gather (Sec. 2, "Hierarchization as preprocessing"): sparse[p] = sum over
+ * the grids containing p of c_g * alpha_g(p), added in grid enumeration order
+ * in fp64, starting from 0.  The grids must hold surpluses (hierarchized).
+ * sparse: device array of gbh_plan_sparse_points doubles, subspace-major
+ * layout (blocks of hierarchical subspaces j, lexicographic, j_0 most
+ * significant; inside a block dimension 0 fastest; level 0 = the two
+ * boundary points).  Works for GBH_F32 grids too (read and promoted).
+ */
+int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream);
+
+/* Sticky device-side status of a plan (GBH_ETIMEOUT after an expired wait);
+ * synchronises the stream given.  Reading it clears it. */
+int gbh_plan_status(gbh_plan *plan, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Human-readable name of a status code (static string). */
+const char *gbh_status_string(int status);
+
+/* Count of kernels this library has launched in this process. */
+int gbh_launch_count(uint64_t *out);
+
+/*
+ * Kernel timing.  While enabled, the library brackets each of its kernel
+ * launches with a pair of CUDA events recorded on the launch stream and
+ * accumulates the durations per kernel name.  gbh_profile_read synchronises
+ * on the recorded events, then reports entry `idx` (0-based; GBH_ERANGE past
+ * the last): its name (copied into name_buf, NUL-terminated, truncated to
+ * buf_len), its launch count and its summed duration in milliseconds.
+ * gbh_profile_reset drops every entry and pending event.
+ */
+int gbh_profile_enable(int on);
+int gbh_profile_read(int idx, char *name_buf, int buf_len, uint64_t *launches, double *total_ms,
+                     double *total_bytes);
+int gbh_profile_reset(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int gbh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBH_H */

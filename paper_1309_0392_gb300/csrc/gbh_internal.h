@@ -1,0 +1,60 @@
+// Internal declarations shared by the translation units of libgbh.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbh.h"
+
+namespace gbh {
+
+constexpr int kMaxDim = 16;
+constexpr int kMaxLevel = 30;
+
+// Geometry of one grid: levels, extents n_k = 2^{l_k}+1, strides S_k.
+struct Geom {
+    int d;
+    int l[kMaxDim];
+    int64_t n[kMaxDim];
+    int64_t S[kMaxDim];
+    int64_t N;       // points of one grid
+    int64_t batch;   // grids of this shape stored back to back (>= 1)
+    int64_t total;   // batch * N
+};
+
+// Validates (d, levels) and fills g; returns GBH_OK or an error status.
+int make_geom(int d, const int32_t *levels, int elem_size, Geom *g);
+
+// Adds `k` to the process-wide count of kernels launched by the library.
+void count_launches(uint64_t k);
+
+// Optional per-launch event timing (gbh_profile_*): construct before a launch,
+// call done() after it.  Does nothing while profiling is off.
+class ProfScope {
+  public:
+    ProfScope(const char *name, cudaStream_t s, double alg_bytes);
+    void done();
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    double bytes_;
+    void *ev0_ = nullptr;
+};
+
+// Maps the last CUDA error (if any) to a status; clears sticky-free errors.
+int check_launch();
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// Plain path: one sweep per dimension with native arithmetic.
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s);
+
+// Fused path: dyadic tiles (class-ordered), see fused.cu.
+int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,
+                    cudaStream_t s);
+
+// True if the fused path supports this (geometry, dtype, op).
+bool fused_supported(const Geom &g, int dtype, int op);
+
+}  // namespace gbh

@@ -1,0 +1,104 @@
+"""Combination-scheme plans: batched transform of many grids in one persistent
+launch, and the fp64 gather into the sparse grid (Sec. 2)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+
+class Plan:
+    """Owns a gbh_plan (device work tables); the grids stay the caller's."""
+
+    def __init__(self, handle, d, dtype_code):
+        self._h = handle
+        self.d = d
+        self.dtype_code = dtype_code
+        self._bound = None
+
+    @classmethod
+    def scheme(cls, d: int, n: int, dtype="float64"):
+        code = _lib.GBH_F64 if str(dtype).endswith("float64") else _lib.GBH_F32
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().gbh_plan_create_scheme(d, n, code, ctypes.byref(h)), "gbh_plan_create_scheme")
+        return cls(h, d, code)
+
+    @classmethod
+    def from_levels(cls, levels, dtype="float64"):
+        lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+        g, d = lv.shape
+        code = _lib.GBH_F64 if str(dtype).endswith("float64") else _lib.GBH_F32
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib().gbh_plan_create(g, d, lv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                              code, ctypes.byref(h)), "gbh_plan_create")
+        return cls(h, d, code)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.lib().gbh_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_grids(self) -> int:
+        v = ctypes.c_int(0)
+        _lib.check(_lib.lib().gbh_plan_num_grids(self._h, ctypes.byref(v)), "gbh_plan_num_grids")
+        return int(v.value)
+
+    def levels(self):
+        out = np.zeros((self.num_grids, self.d), dtype=np.int32)
+        for g in range(out.shape[0]):
+            _lib.check(_lib.lib().gbh_plan_grid_levels(
+                self._h, g, out[g].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "gbh_plan_grid_levels")
+        return out
+
+    def coeffs(self):
+        out = np.zeros(self.num_grids, dtype=np.float64)
+        _lib.check(_lib.lib().gbh_plan_coeffs(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                   "gbh_plan_coeffs")
+        return out
+
+    @property
+    def sparse_points(self) -> int:
+        v = ctypes.c_int64(0)
+        _lib.check(_lib.lib().gbh_plan_sparse_points(self._h, ctypes.byref(v)), "gbh_plan_sparse_points")
+        return int(v.value)
+
+    @property
+    def total_points(self) -> int:
+        v = ctypes.c_int64(0)
+        _lib.check(_lib.lib().gbh_plan_total_points(self._h, ctypes.byref(v)), "gbh_plan_total_points")
+        return int(v.value)
+
+    def bind(self, grids, stream=None):
+        """Bind device tensors (one per grid, in plan order)."""
+        import torch
+        ptrs = (ctypes.c_void_p * len(grids))(*[ctypes.c_void_p(t.data_ptr()) for t in grids])
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(_lib.lib().gbh_plan_bind(self._h, ptrs, ctypes.c_void_p(s.cuda_stream)), "gbh_plan_bind")
+        self._bound = list(grids)
+
+    def execute(self, op=_lib.GBH_HIERARCHIZE, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(_lib.lib().gbh_plan_execute(self._h, int(op), ctypes.c_void_p(s.cuda_stream)),
+                   "gbh_plan_execute")
+
+    def gather(self, sparse, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(_lib.lib().gbh_plan_gather(self._h, ctypes.c_void_p(sparse.data_ptr()),
+                                              ctypes.c_void_p(s.cuda_stream)), "gbh_plan_gather")
+        return sparse
+
+    def status(self, stream=None) -> int:
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return int(_lib.lib().gbh_plan_status(self._h, ctypes.c_void_p(s.cuda_stream)))

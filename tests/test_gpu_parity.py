@@ -1,0 +1,123 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+fp64 plain path: the kernels apply the serial operation order, so results are
+bit-identical to the oracle.  Every other fp64 path: within 1e-13 relative to
+max|u|.  fp32: within 1e-5 relative to max|u| against the oracle run on the
+same fp32 input promoted to fp64.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import load
+from paper_1309_0392_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+gbh = pytest.importorskip("paper_1309_0392_gb300")
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}
+ORACLE = {"h": oracle.hierarchize, "d": oracle.dehierarchize, "a": oracle.hierarchize_adjoint}
+TOL64 = 1e-13
+TOL32 = 1e-5
+
+
+def run(u, levels, op, dtype=torch.float64, **kw):
+    t = torch.tensor(u, dtype=dtype, device="cuda")
+    gbh.transform(t, levels, OPS[op], **kw)
+    torch.cuda.synchronize()
+    return t.cpu().double().numpy()
+
+
+def rel_err(a, b, u):
+    return np.abs(a - b).max() / max(np.abs(u).max(), 1e-300)
+
+
+@pytest.mark.parametrize("op,name", [("h", "cfg1a_hierarchize.txt"), ("d", "cfg1a_dehierarchize.txt"),
+                                     ("a", "cfg1a_adjoint.txt")])
+@pytest.mark.parametrize("path", [gbh.GBH_PATH_PLAIN, gbh.GBH_PATH_AUTO])
+def test_cfg1a_golden(op, name, path):
+    levels, u = inputs.cfg1a()
+    got = run(u, levels, op, path=path)
+    ref = load(name)
+    if path == gbh.GBH_PATH_PLAIN:
+        assert np.array_equal(got, ref)
+    else:
+        assert rel_err(got, ref, u) <= TOL64
+
+
+@pytest.mark.parametrize("path", [gbh.GBH_PATH_PLAIN, gbh.GBH_PATH_AUTO])
+def test_cfg1b_closed_form_bit_exact(path):
+    levels, u = inputs.cfg1b()
+    assert np.array_equal(run(u, levels, "h", path=path), load("cfg1b_hierarchize.txt"))
+
+
+def random_levels(rng, count):
+    out = []
+    for _ in range(count):
+        d = int(rng.integers(1, 7))
+        budget = 16 if d <= 3 else 14
+        lv = []
+        for _ in range(d):
+            lv.append(int(rng.integers(0, 9)))
+        while sum(lv) > budget:
+            k = int(np.argmax(lv))
+            lv[k] -= 1
+        out.append(tuple(lv))
+    return out
+
+
+LEVELS = [(1,), (5,), (12,), (3, 4), (9, 0), (0, 9), (1, 1, 1), (5, 4, 4), (4, 6, 3), (2, 3, 1, 4),
+          (3, 3, 2, 2, 2), (1, 2, 1, 2, 1, 2)] + random_levels(np.random.default_rng(2024), 12)
+
+
+@pytest.mark.parametrize("levels", LEVELS)
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_plain_fp64_bit_exact(levels, op):
+    u = inputs.uniform(levels, 100 + len(levels))
+    assert np.array_equal(run(u, levels, op, path=gbh.GBH_PATH_PLAIN), ORACLE[op](u, levels))
+
+
+@pytest.mark.parametrize("levels", LEVELS)
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_auto_fp64(levels, op):
+    u = inputs.uniform(levels, 200 + len(levels))
+    assert rel_err(run(u, levels, op), ORACLE[op](u, levels), u) <= TOL64
+
+
+@pytest.mark.parametrize("levels", LEVELS)
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+@pytest.mark.parametrize("path", [gbh.GBH_PATH_PLAIN, gbh.GBH_PATH_AUTO])
+def test_fp32(levels, op, path):
+    u32 = inputs.uniform(levels, 300 + len(levels), dtype=np.float32)
+    u = u32.astype(np.float64)
+    assert rel_err(run(u32, levels, op, dtype=torch.float32, path=path), ORACLE[op](u, levels), u) <= TOL32
+
+
+@pytest.mark.parametrize("levels", [(16,), (15,), (2, 13), (1, 1, 14), (14, 1, 1, 1)])
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_long_poles(levels, op):
+    """Rows longer than the staged-row limit and dimensions with few long
+    poles take the per-level kernels."""
+    u = inputs.uniform(levels, 7)
+    assert np.array_equal(run(u, levels, op, path=gbh.GBH_PATH_PLAIN), ORACLE[op](u, levels))
+    assert rel_err(run(u, levels, op), ORACLE[op](u, levels), u) <= TOL64
+
+
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_same_shape_batch(op):
+    levels, B = (4, 3, 5), 5
+    n = inputs.num_points(levels)
+    u = np.random.default_rng(3).uniform(-1, 1, (B, n))
+    got = run(u.reshape(-1), levels, op, batch=B).reshape(B, n)
+    for b in range(B):
+        assert rel_err(got[b], ORACLE[op](u[b], levels), u[b]) <= TOL64
+
+
+def test_degenerate_level_zero():
+    """All-boundary grids (every level 0) are unchanged by every op."""
+    levels = (0, 0, 0)
+    u = inputs.uniform(levels, 1)
+    for op in "hda":
+        assert np.array_equal(run(u, levels, op), u)
