@@ -133,6 +133,13 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
  */
 int gbh_num_points(int d, const int32_t *levels, int64_t *out);
 
+/*
+ * Tile exponents the fused path would use for (d, levels, dtype, op): the
+ * planner's choice, written to m_out[0..d-1].  Host only (no device work).
+ * GBH_EUNSUPPORTED if the fused path does not take this shape.
+ */
+int gbh_tile_plan(int d, const int32_t *levels, int dtype, int op, int32_t *m_out);
+
 /* ------------------------------------------------------------------------ */
 /* Combination scheme (Sec. 2): batched transform and sparse-grid gather     */
 /* ------------------------------------------------------------------------ */

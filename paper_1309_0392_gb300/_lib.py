@@ -47,6 +47,7 @@ _SIGS = {
     "gbh_transform_batched": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, _I32P, ctypes.c_int,
                                              ctypes.c_int, ctypes.POINTER(Options), _VP]),
     "gbh_num_points": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.POINTER(ctypes.c_int64)]),
+    "gbh_tile_plan": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int, _I32P]),
     "gbh_plan_create_scheme": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(_VP)]),
     "gbh_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P, ctypes.c_int,
@@ -137,3 +138,14 @@ def profile_read():
         out[buf.value.decode()] = (int(n.value), float(ms.value), float(by.value))
         i += 1
     return out
+
+
+def tile_plan(levels, dtype_code=GBH_F64, op=GBH_HIERARCHIZE):
+    """Tile exponents the fused path chooses for this shape (None if it does
+    not take the shape).  Host only."""
+    out = (ctypes.c_int32 * len(levels))()
+    st = lib().gbh_tile_plan(len(levels), levels_arg(levels), dtype_code, op, out)
+    if st == -8:
+        return None
+    check(st, "gbh_tile_plan")
+    return tuple(int(v) for v in out)

@@ -130,6 +130,18 @@ int gbh_num_points(int d, const int32_t *levels, int64_t *out)
     return GBH_OK;
 }
 
+int gbh_tile_plan(int d, const int32_t *levels, int dtype, int op, int32_t *m_out)
+{
+    if (!m_out) return GBH_EINVAL;
+    if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
+    Geom g;
+    if (int e = make_geom(d, levels, dtype == GBH_F64 ? 8 : 4, &g)) return e;
+    int m[kMaxDim] = {0};
+    if (!fused_tiles(g, dtype, op, m)) return GBH_EUNSUPPORTED;
+    for (int k = 0; k < d; ++k) m_out[k] = m[k];
+    return GBH_OK;
+}
+
 int gbh_transform(void *data, int d, const int32_t *levels, int dtype, int op,
                   const gbh_options *opt, void *stream)
 {
@@ -158,7 +170,10 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
         if (!fused_supported(g, dtype, op)) return GBH_EUNSUPPORTED;
         return fused_transform(data, g, dtype, op, opt, s);
     }
-    if (fused_supported(g, dtype, op)) return fused_transform(data, g, dtype, op, opt, s);
+    // planner's choice: the fused path when it takes the shape and the grid is
+    // large enough to tile, else one sweep per dimension
+    int m[kMaxDim] = {0};
+    if (g.N >= 4096 && fused_tiles(g, dtype, op, m)) return fused_transform(data, g, dtype, op, opt, s);
     return plain_transform(data, g, dtype, op, s);
 }
 

@@ -1,13 +1,848 @@
-// Fused path (dyadic tiles): not built yet.
+// Fused path: every dimension of a grid in one shared-memory round trip per
+// tile, in place, without scratch memory.
+//
+// Dyadic split (derived from the predecessor structure of Alg. 1, Sec. 3).
+// Pick a tile exponent m_k per dimension and write i_k = a 2^{m_k} + r_k.  A
+// point with r_k != 0 has both predecessors inside its dyadic block
+// [a 2^{m_k}, (a+1) 2^{m_k}]; a point with r_k = 0 (a "lattice" point) has
+// lattice predecessors only.  Give every point the class C = {k : r_k = 0}.
+// The surplus of a class-C point depends only on the values of points of
+// classes containing C inside its "closure": the block closure in the
+// dimensions outside C times the lattice in the dimensions of C.  On that
+// closure it is the ordinary hierarchization of a small dense grid (levels
+// m_k outside C, l_k - m_k inside C).
+//
+// In-place schedule.  Hierarchization reads only classes containing C, so the
+// classes are processed by increasing |C| (one launch per |C|): when class C
+// is written, every reader of its nodal values has finished.  The inverse goes
+// the other way (|C| decreasing): class C reads final nodal values on the
+// closure faces and surpluses inside.  A lattice dimension whose closure would
+// not fit in shared memory becomes a "point" dimension: the closure is taken
+// at one lattice position and the lattice transform along that dimension is
+// applied by a separate strided pass over the class's points.
+//
+// Arithmetic.  fp32 grids compute in fp32.  fp64 grids compute in exact int64
+// block fixed point by default: GB300 issues fp64 instructions at about 1/64
+// of the fp32 rate, so fp64 arithmetic, not HBM, would bound the sweep.  Each
+// closure is scaled by its largest binary exponent; hierarchization uses the
+// doubling form 2u - L - R (exact, no rounding at all), dehierarchization adds
+// halved predecessor sums; the result is rounded to fp64 once.  Inputs are
+// truncated to 2^{-(g0-1)} of the closure's largest magnitude, far below the
+// fp64 rounding of the serial algorithm.  Inputs must be finite; subnormal
+// inputs count as zero.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
 #include "gbh_internal.h"
 
 namespace gbh {
+namespace {
 
-bool fused_supported(const Geom &, int, int) { return false; }
+constexpr int kFD = 6;            // dimensions handled by the fused path
+// largest closure extent (poles are held in registers): 65 for 4-byte
+// values, 33 for 8-byte values
+__host__ __device__ constexpr int max_extent(int value_bytes) { return value_bytes == 8 ? 33 : 65; }
+constexpr int kMaxCls = 20;       // classes of one |C| (C(6,3))
+constexpr int kThreads = 256;
 
-int fused_transform(void *, const Geom &, int, int, const gbh_options *, cudaStream_t)
+enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
+enum Mode { BLOCK = 0, LATTICE = 1, POINT = 2 };
+
+// One class of one grid shape.
+struct ClassDesc {
+    int e[kFD];          // closure extent per dimension
+    unsigned mag[kFD];   // __umulhi magic of e[k]
+    int ss[kFD];         // shared-memory stride
+    int mode[kFD];
+    int lev[kFD];        // local transform level (0 = no pass)
+    int we[kFD];         // write-box extent
+    int wlo[kFD];        // write-box start
+    unsigned wmag[kFD];  // __umulhi magic of we[k]
+    int64_t gstride[kFD];  // global element stride of one closure step
+    int64_t gstep[kFD];    // global element offset of one group step
+    int64_t ngrp[kFD];     // groups along each dimension
+    int64_t groups;
+    int64_t grp_base;    // first group of this class within the launch
+    int V;               // closure points
+    int rows;            // V / e[0]
+    int W;               // write-box points
+    int wrows;           // W / we[0]
+    int g0;              // fixed point: bits of the input scale
+    int doublings;       // fixed point: doubling passes (hierarchization)
+};
+
+struct LaunchParams {
+    int d;
+    int ncls;
+    int64_t per_grid;    // groups of one grid (sum over classes)
+    int64_t total;       // per_grid * batch
+    int64_t N;           // points per grid (batch stride)
+    int off_wg;          // byte offsets in dynamic shared memory: write-row
+    int off_ws;          //   global bases, write-row shared bases, values
+    int off_vals;
+    ClassDesc cls[kMaxCls];
+};
+
+__host__ __device__ inline unsigned magic_of(int e) { return (unsigned)(0xFFFFFFFFu / (unsigned)e) + 1u; }
+__device__ __forceinline__ int udiv(int n, unsigned mag) { return (int)__umulhi((unsigned)n, mag); }
+
+// ---------------------------------------------------------------------------
+// fixed point <-> fp64
+// ---------------------------------------------------------------------------
+
+// v = sign * M * 2^{c - (emax - e)}, M the 53-bit significand: the input scaled
+// so that the largest magnitude of the closure sits just below 2^{g0}.
+__device__ __forceinline__ long long to_fixed(long long bits, int emax, int c)
 {
-    return GBH_EUNSUPPORTED;
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = c - (emax - e);
+    long long v;
+    if (e == 0) v = 0;
+    else if (sh >= 0) v = (long long)(M << sh);
+    else v = (-sh >= 63) ? 0 : (long long)(M >> (-sh));
+    return bits < 0 ? -v : v;
+}
+
+// v * 2^X rounded to fp64 once (the integer-to-fp64 conversion rounds; the
+// power of two is exact unless the result leaves the normal range).
+__device__ __forceinline__ double from_fixed(long long v, int X)
+{
+    if (v == 0) return 0.0;
+    const double r = __ll2double_rn(v);
+    const long long b = __double_as_longlong(r);
+    const int ne = (int)((b >> 52) & 0x7FF) + X;
+    if (ne > 0 && ne < 2047) return __longlong_as_double(b + ((long long)X << 52));
+    return ldexp(r, X);
+}
+
+// ---------------------------------------------------------------------------
+// 1-D pole operations on a register copy of a shared-memory pole
+// ---------------------------------------------------------------------------
+
+enum PoleOp { P_H_DBL, P_H_HALF, P_D_FIX, P_H_NAT, P_D_NAT };
+
+template <int E>
+struct LevelOf { static constexpr int v = (E <= 2) ? 0 : 1 + LevelOf<(E + 1) / 2>::v; };
+template <>
+struct LevelOf<1> { static constexpr int v = 0; };
+
+template <typename V, int E, int PO>
+__device__ __forceinline__ void pole_regs(V *v)
+{
+    constexpr int L = LevelOf<E>::v;
+    constexpr int last = 1 << L;
+    if constexpr (PO == P_H_DBL || PO == P_H_HALF || PO == P_H_NAT) {
+#pragma unroll
+        for (int lev = L; lev >= 1; --lev) {
+            const int s = 1 << (L - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) {
+                if constexpr (PO == P_H_DBL) v[i] = (v[i] + v[i]) - v[i - s] - v[i + s];
+                else if constexpr (PO == P_H_HALF) v[i] = v[i] - ((v[i - s] + v[i + s]) >> 1);
+                else v[i] = v[i] - V(0.5) * (v[i - s] + v[i + s]);
+            }
+        }
+        if constexpr (PO == P_H_DBL) {
+            v[0] = v[0] + v[0];
+            v[last] = v[last] + v[last];
+        }
+    } else {
+#pragma unroll
+        for (int lev = 1; lev <= L; ++lev) {
+            const int s = 1 << (L - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) {
+                if constexpr (PO == P_D_FIX) v[i] = v[i] + ((v[i - s] + v[i + s]) >> 1);
+                else v[i] = v[i] + V(0.5) * (v[i - s] + v[i + s]);
+            }
+        }
+    }
+}
+
+template <typename V, int E, int PO>
+__device__ __forceinline__ void pole_smem(V *s, int st)
+{
+    V v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = s[i * st];
+    pole_regs<V, E, PO>(v);
+#pragma unroll
+    for (int i = 0; i < E; ++i) s[i * st] = v[i];
+}
+
+template <typename V, int PO>
+__device__ __forceinline__ void pole_dispatch(V *s, int st, int e)
+{
+    switch (e) {
+        case 3: pole_smem<V, 3, PO>(s, st); break;
+        case 5: pole_smem<V, 5, PO>(s, st); break;
+        case 9: pole_smem<V, 9, PO>(s, st); break;
+        case 17: pole_smem<V, 17, PO>(s, st); break;
+        case 33: pole_smem<V, 33, PO>(s, st); break;
+        case 65:
+            if constexpr (max_extent(sizeof(V)) >= 65) pole_smem<V, 65, PO>(s, st);
+            break;
+        default: break;
+    }
+}
+
+// Which poles of a pass: all, those whose other block coordinates are all
+// interior, or those with some other block coordinate on the block boundary.
+enum PoleSet { ALL = 0, INTERIOR = 1, FACE = 2 };
+
+template <typename V, int PO>
+__device__ void pass_dim(V *vals, const ClassDesc &C, int d, int k, int set)
+{
+    const int ek = C.e[k];
+    const int npoles = C.V / ek;
+    for (int p = threadIdx.x; p < npoles; p += blockDim.x) {
+        int rem = p, off = 0;
+        bool interior = true;
+#pragma unroll
+        for (int j = 0; j < kFD; ++j) {
+            if (j >= d || j == k) continue;
+            const int q = udiv(rem, C.mag[j]);
+            const int c = rem - q * C.e[j];
+            rem = q;
+            off += c * C.ss[j];
+            if (C.mode[j] == BLOCK && (c == 0 || c == C.e[j] - 1)) interior = false;
+        }
+        if (set == INTERIOR && !interior) continue;
+        if (set == FACE && interior) continue;
+        pole_dispatch<V, PO>(vals + off, C.ss[k], ek);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// closure kernel
+// ---------------------------------------------------------------------------
+
+// ST: storage type; FIX: int64 fixed-point arithmetic (fp64 storage only).
+template <typename ST, bool FIX, int OP>
+__global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__ LaunchParams P,
+                                                      ST *__restrict__ u)
+{
+    using V = typename std::conditional<FIX, long long, ST>::type;
+    extern __shared__ __align__(16) unsigned char sm[];
+    int64_t *rowg = reinterpret_cast<int64_t *>(sm);           // global base of every closure row
+    int64_t *s_wg = reinterpret_cast<int64_t *>(sm + P.off_wg); // global base of every write row
+    int *s_ws = reinterpret_cast<int *>(sm + P.off_ws);         // shared base of every write row
+    V *vals = reinterpret_cast<V *>(sm + P.off_vals);
+    __shared__ int s_emax;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int d = P.d;
+
+    for (int64_t G = blockIdx.x; G < P.total; G += gridDim.x) {
+        const int64_t b = G / P.per_grid;
+        const int64_t gl = G - b * P.per_grid;
+        int c = 0;
+        while (c + 1 < P.ncls && gl >= P.cls[c + 1].grp_base) ++c;
+        const ClassDesc &C = P.cls[c];
+        // group coordinates -> global base of the closure
+        int64_t g = gl - C.grp_base;
+        int64_t base = b * P.N;
+#pragma unroll
+        for (int k = 0; k < kFD; ++k) {
+            if (k >= d) break;
+            const int64_t q = g / C.ngrp[k];
+            base += (g - q * C.ngrp[k]) * C.gstep[k];
+            g = q;
+        }
+        // row tables: closure rows (global base) and write rows
+        for (int r = tid; r < C.rows; r += T) {
+            int rem = r;
+            int64_t off = base;
+#pragma unroll
+            for (int k = 1; k < kFD; ++k) {
+                if (k >= d) break;
+                const int q = udiv(rem, C.mag[k]);
+                off += (int64_t)(rem - q * C.e[k]) * C.gstride[k];
+                rem = q;
+            }
+            rowg[r] = off;
+        }
+        for (int r = tid; r < C.wrows; r += T) {
+            int rem = r, crow = 0, rstride = 1;
+#pragma unroll
+            for (int k = 1; k < kFD; ++k) {
+                if (k >= d) break;
+                const int q = udiv(rem, C.wmag[k]);
+                crow += (rem - q * C.we[k] + C.wlo[k]) * rstride;
+                rstride *= C.e[k];
+                rem = q;
+            }
+            s_ws[r] = crow * C.e[0] + C.wlo[0];
+            s_wg[r] = crow;       // closure row; global base filled below
+        }
+        if (tid == 0) s_emax = 0;
+        __syncthreads();
+        for (int r = tid; r < C.wrows; r += T) s_wg[r] = rowg[s_wg[r]] + (int64_t)C.wlo[0] * C.gstride[0];
+
+        // load the closure
+        int emax = 0;
+        {
+            const int e0 = C.e[0];
+            const int64_t gs0 = C.gstride[0];
+            constexpr int U = 8;
+            for (int e = tid; e < C.V; e += T * U) {
+                ST tmp[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int ee = e + q * T;
+                    if (ee < C.V) {
+                        const int r = udiv(ee, C.mag[0]);
+                        tmp[q] = u[rowg[r] + (int64_t)(ee - r * e0) * gs0];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int ee = e + q * T;
+                    if (ee < C.V) {
+                        if constexpr (FIX) {
+                            const long long bits = __double_as_longlong((double)tmp[q]);
+                            const int ex = (int)((bits >> 52) & 0x7FF);
+                            emax = ex > emax ? ex : emax;
+                            vals[ee] = (V)bits;
+                        } else {
+                            vals[ee] = (V)tmp[q];
+                        }
+                    }
+                }
+            }
+        }
+        int X = 0;
+        if constexpr (FIX) {
+            emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+            if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+            __syncthreads();
+            emax = s_emax;
+            const int cshift = C.g0 - 53;
+            for (int e = tid; e < C.V; e += T) vals[e] = (V)to_fixed((long long)vals[e], emax, cshift);
+            X = emax - 1075 - cshift - (OP == OP_H ? C.doublings : 0);
+        }
+        __syncthreads();
+
+        // transform
+        if constexpr (OP == OP_H) {
+            for (int k = 0; k < d; ++k) {
+                if (C.lev[k] == 0) continue;
+                pass_dim<V, FIX ? P_H_DBL : P_H_NAT>(vals, C, d, k, ALL);
+                __syncthreads();
+            }
+        } else {
+            // lattice dimensions: surpluses -> partial nodal values, interior poles only
+            for (int k = 0; k < d; ++k) {
+                if (C.lev[k] == 0 || C.mode[k] != LATTICE) continue;
+                pass_dim<V, FIX ? P_D_FIX : P_D_NAT>(vals, C, d, k, INTERIOR);
+                __syncthreads();
+            }
+            // block faces hold final nodal values: hierarchize them in the
+            // block dimensions, so the closure holds one consistent vector
+            for (int k = 0; k < d; ++k) {
+                if (C.lev[k] == 0 || C.mode[k] != BLOCK) continue;
+                pass_dim<V, FIX ? P_H_HALF : P_H_NAT>(vals, C, d, k, FACE);
+                __syncthreads();
+            }
+            for (int k = 0; k < d; ++k) {
+                if (C.lev[k] == 0 || C.mode[k] != BLOCK) continue;
+                pass_dim<V, FIX ? P_D_FIX : P_D_NAT>(vals, C, d, k, ALL);
+                __syncthreads();
+            }
+        }
+
+        // write the class's points
+        {
+            const int we0 = C.we[0];
+            const int64_t gs0 = C.gstride[0];
+            for (int e = tid; e < C.W; e += T) {
+                const int r = udiv(e, C.wmag[0]);
+                const int x = e - r * we0;
+                const V v = vals[s_ws[r] + x];
+                ST out;
+                if constexpr (FIX) out = (ST)from_fixed((long long)v, X);
+                else out = (ST)v;
+                u[s_wg[r] + (int64_t)x * gs0] = out;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// lattice pass: transform along one point dimension of a class, native
+// arithmetic, one thread per lattice pole (all other coordinates fixed)
+// ---------------------------------------------------------------------------
+
+struct LatticeParams {
+    int d;
+    int k;                 // pole dimension
+    int lev;               // pole level (l_k - m_k)
+    int64_t pstride;       // 2^{m_k} S_k
+    int kind[kFD];         // 0: block-interior positions, 1: lattice positions
+    int64_t cnt[kFD];      // positions per dimension (1 for k)
+    int64_t m_pow[kFD];    // 2^{m_j}
+    int64_t S[kFD];
+    int64_t poles;         // per grid
+    int64_t total;         // poles * batch
+    int64_t N;
+};
+
+template <typename ST, int OP>
+__global__ void __launch_bounds__(kThreads) k_lattice(const __grid_constant__ LatticeParams L, ST *__restrict__ u)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L.total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = t / L.poles;
+        int64_t p = t - b * L.poles;
+        int64_t off = b * L.N;
+        for (int j = 0; j < L.d; ++j) {
+            if (j == L.k) continue;
+            const int64_t q = p / L.cnt[j];
+            const int64_t pos = p - q * L.cnt[j];
+            p = q;
+            int64_t coord;
+            if (L.kind[j] == 0) {
+                const int64_t w = L.m_pow[j] - 1;
+                const int64_t blk = pos / w;
+                coord = blk * L.m_pow[j] + (pos - blk * w) + 1;
+            } else {
+                coord = pos * L.m_pow[j];
+            }
+            off += coord * L.S[j];
+        }
+        ST *pp = u + off;
+        const int64_t last = (int64_t)1 << L.lev;
+        const int64_t S = L.pstride;
+        if (OP == OP_H) {
+            for (int lev = L.lev; lev >= 1; --lev) {
+                const int64_t s = (int64_t)1 << (L.lev - lev);
+                for (int64_t i = s; i < last; i += 2 * s)
+                    pp[i * S] = pp[i * S] - ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
+            }
+        } else {
+            for (int lev = 1; lev <= L.lev; ++lev) {
+                const int64_t s = (int64_t)1 << (L.lev - lev);
+                for (int64_t i = s; i < last; i += 2 * s)
+                    pp[i * S] = pp[i * S] + ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host planner
+// ---------------------------------------------------------------------------
+
+// Largest row sum of |weights| of the 1-D nodal evaluation of a level-lev pole
+// (how much dehierarchization can grow a vector in the max norm).
+double dehier_growth(int lev)
+{
+    const int n = (1 << lev) + 1;
+    double best = 0.0;
+    for (int i = 0; i < n; ++i) {
+        // nodal value at i of unit surpluses of absolute weight: sum of hats
+        const double x = (double)i / (double)(n - 1);
+        double s = 1.0;   // the two boundary hats sum to one
+        for (int j = 1; j <= lev; ++j) {
+            const int st = 1 << (lev - j);
+            const int a = (i / (2 * st)) * (2 * st) + st;
+            if (a >= n - 1) continue;
+            const double w = 1.0 - std::fabs((double)(i - a)) / (double)st;
+            if (w > 0) s += w;
+        }
+        (void)x;
+        best = std::max(best, s);
+    }
+    return best;
+}
+
+struct ClassPlan {
+    unsigned mask;
+    ClassDesc desc;
+    int point_dims[kFD];
+    int npoint;
+    size_t smem;
+};
+
+struct Plan {
+    int d;
+    int m[kFD];
+    std::vector<std::vector<ClassPlan>> by_size;   // index |C|
+};
+
+int popc(unsigned x) { return __builtin_popcount(x); }
+
+size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+size_t closure_smem(const ClassDesc &c, int es)
+{
+    return al16((size_t)c.rows * 8) + al16((size_t)c.wrows * 8) + al16((size_t)c.wrows * 4) + (size_t)c.V * es;
+}
+
+// Builds the closure descriptor of class `mask`; returns false if the class
+// has no points.  Lattice dimensions are turned into point dimensions (the
+// largest first) until the closure fits `cap` bytes and every extent <= 65.
+bool make_class(const Geom &g, const int *m, unsigned mask, int es, size_t cap, int op, ClassPlan *out)
+{
+    const int d = g.d;
+    ClassPlan cp{};
+    cp.mask = mask;
+    ClassDesc &c = cp.desc;
+    for (int k = 0; k < d; ++k) {
+        const bool inC = (mask >> k) & 1u;
+        if (!inC && m[k] == 0) return false;          // no block interior: empty class
+        if (inC) {
+            c.mode[k] = LATTICE;
+            c.e[k] = (1 << (g.l[k] - m[k])) + 1;
+            c.lev[k] = g.l[k] - m[k];
+            c.gstride[k] = ((int64_t)1 << m[k]) * g.S[k];
+            c.gstep[k] = 0;
+            c.ngrp[k] = 1;
+            c.we[k] = c.e[k];
+            c.wlo[k] = 0;
+        } else {
+            c.mode[k] = BLOCK;
+            c.e[k] = (1 << m[k]) + 1;
+            c.lev[k] = m[k];
+            c.gstride[k] = g.S[k];
+            c.gstep[k] = ((int64_t)1 << m[k]) * g.S[k];
+            c.ngrp[k] = (int64_t)1 << (g.l[k] - m[k]);
+            c.we[k] = c.e[k] - 2;
+            c.wlo[k] = 1;
+        }
+    }
+    auto to_point = [&](int k) {
+        c.mode[k] = POINT;
+        const int ext = (1 << (g.l[k] - m[k])) + 1;
+        c.e[k] = 1;
+        c.lev[k] = 0;
+        c.ngrp[k] = ext;
+        c.gstep[k] = ((int64_t)1 << m[k]) * g.S[k];
+        c.we[k] = 1;
+        c.wlo[k] = 0;
+    };
+    for (int k = 0; k < d; ++k)
+        if (c.mode[k] == LATTICE && c.e[k] > max_extent(es)) to_point(k);
+    auto volume = [&]() {
+        int64_t v = 1;
+        for (int k = 0; k < d; ++k) v *= c.e[k];
+        return v;
+    };
+    auto wvolume = [&]() {
+        int64_t v = 1;
+        for (int k = 1; k < d; ++k) v *= (c.mode[k] == BLOCK ? c.e[k] - 2 : c.e[k]);
+        return v;
+    };
+    for (;;) {
+        c.V = (int)std::min<int64_t>(volume(), INT32_MAX);
+        c.rows = c.V / c.e[0];
+        c.wrows = (int)std::min<int64_t>(wvolume(), INT32_MAX);
+        if (closure_smem(c, es) <= cap) break;
+        int best = -1;
+        for (int k = 0; k < d; ++k)
+            if (c.mode[k] == LATTICE && (best < 0 || c.e[k] > c.e[best])) best = k;
+        if (best < 0) return false;                     // block closure alone too big
+        to_point(best);
+    }
+    int ss = 1;
+    c.W = 1;
+    for (int k = 0; k < d; ++k) {
+        c.ss[k] = ss;
+        ss *= c.e[k];
+        c.mag[k] = magic_of(c.e[k]);
+        c.wmag[k] = magic_of(c.we[k]);
+        c.W *= c.we[k];
+    }
+    c.wrows = c.W / c.we[0];
+    c.groups = 1;
+    for (int k = 0; k < d; ++k) c.groups *= c.ngrp[k];
+    // fixed-point headroom
+    int passes = 0;
+    double growth = 1.0;
+    for (int k = 0; k < d; ++k) {
+        if (c.lev[k] == 0) continue;
+        ++passes;
+        if (op == OP_D) growth *= (c.mode[k] == BLOCK ? 2.0 : 1.0) * dehier_growth(c.lev[k]);
+    }
+    c.doublings = passes;
+    if (op == OP_H) c.g0 = 61 - 2 * passes;
+    else c.g0 = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
+    cp.npoint = 0;
+    for (int k = 0; k < d; ++k)
+        if (c.mode[k] == POINT) cp.point_dims[cp.npoint++] = k;
+    cp.smem = closure_smem(c, es);
+    *out = cp;
+    return true;
+}
+
+// Estimated DRAM bytes of one transform with tile exponents m.
+double estimate_bytes(const Geom &g, const int *m, int es, int op, size_t cap, bool *ok)
+{
+    const int d = g.d;
+    double bytes = 0.0;
+    *ok = true;
+    for (unsigned mask = 0; mask < (1u << d); ++mask) {
+        ClassPlan cp;
+        if (!make_class(g, m, mask, es, mask == 0 ? cap / 2 : cap, op, &cp)) {
+            bool empty = false;
+            for (int k = 0; k < d; ++k)
+                if (!((mask >> k) & 1u) && m[k] == 0) empty = true;
+            if (!empty) { *ok = false; return 1e300; }
+            continue;
+        }
+        const ClassDesc &c = cp.desc;
+        // dimension 0 strided (lattice or point): one 32-byte sector per element
+        const bool strided0 = c.mode[0] != BLOCK && m[0] > 0;
+        const double waste0 = strided0 ? std::max(1.0, 32.0 / es) : (c.mode[0] == BLOCK ? (c.e[0] * es + 24.0) / (c.e[0] * es) : 1.0);
+        double points = (double)c.groups * c.W;
+        bytes += (double)c.groups * c.V * es * waste0 + points * es * waste0;
+        for (int i = 0; i < cp.npoint; ++i) {
+            const int k = cp.point_dims[i];
+            const double w = (k == 0 || strided0) ? std::max(1.0, 32.0 / es) : 1.0;
+            bytes += 2.0 * points * es * w;
+        }
+    }
+    return bytes;
+}
+
+std::mutex g_plan_mu;
+std::map<std::vector<int>, Plan> g_plans;
+
+// Tile exponents minimising the estimated DRAM bytes, subject to: every
+// dimension of level >= 1 has a block interior (m_k >= 1); every lattice
+// extent 2^{l_k - m_k} + 1 and block extent 2^{m_k} + 1 fits a register pole;
+// the interior-class closure fits half the shared-memory budget (two CTAs
+// per SM).  Returns false when no such m exists (e.g. one very long
+// dimension): the plain path then takes the grid.
+bool choose_m(const Geom &g, int es, int op, int *m_out)
+{
+    const int d = g.d;
+    const size_t cap = 200 * 1024;
+    const int emax_lev = max_extent(es) == 65 ? 6 : 5;
+    int lo[kFD], hi[kFD], m[kFD];
+    for (int k = 0; k < d; ++k) {
+        if (g.l[k] == 0) { lo[k] = hi[k] = 0; continue; }
+        lo[k] = std::max(1, g.l[k] - emax_lev);
+        hi[k] = std::min(g.l[k], emax_lev);
+        if (lo[k] > hi[k]) return false;
+    }
+    for (int k = 0; k < d; ++k) m[k] = lo[k];
+    double best = 1e300;
+    bool found = false;
+    for (;;) {
+        int64_t vol = 1;
+        for (int k = 0; k < d; ++k) vol *= (int64_t)(1 << m[k]) + 1;
+        if ((size_t)vol * es <= cap / 2) {
+            bool ok;
+            const double b = estimate_bytes(g, m, es, op, cap, &ok);
+            if (ok && b < best) {
+                best = b;
+                found = true;
+                for (int k = 0; k < d; ++k) m_out[k] = m[k];
+            }
+        }
+        int k = 0;
+        while (k < d && ++m[k] > hi[k]) { m[k] = lo[k]; ++k; }
+        if (k == d) break;
+    }
+    return found;
+}
+
+// Class plans for explicit tile exponents m.
+bool build_plan_m(const Geom &g, int es, int op, const int *m, Plan *plan)
+{
+    const int d = g.d;
+    const size_t cap = 200 * 1024;
+    plan->d = d;
+    for (int k = 0; k < d; ++k) plan->m[k] = m[k];
+    plan->by_size.assign(d + 1, {});
+    for (unsigned mask = 0; mask < (1u << d); ++mask) {
+        ClassPlan cp;
+        if (!make_class(g, m, mask, es, mask == 0 ? cap / 2 : cap, op, &cp)) {
+            bool empty = false;
+            for (int k = 0; k < d; ++k)
+                if (!((mask >> k) & 1u) && m[k] == 0) empty = true;
+            if (!empty) return false;
+            continue;
+        }
+        plan->by_size[popc(mask)].push_back(cp);
+    }
+    return true;
+}
+
+// Plan for requested tile exponents (any nonzero entry), else the cached
+// planner choice for this shape.
+bool build_plan(const Geom &g, int es, int op, const int *m_req, Plan *plan)
+{
+    const int d = g.d;
+    bool explicit_m = false;
+    if (m_req)
+        for (int k = 0; k < d; ++k) explicit_m |= m_req[k] != 0;
+    if (explicit_m) {
+        for (int k = 0; k < d; ++k)
+            if (m_req[k] < 0 || m_req[k] > g.l[k] || (1 << m_req[k]) + 1 > max_extent(es)) return false;
+        return build_plan_m(g, es, op, m_req, plan);
+    }
+    std::vector<int> key;
+    key.push_back(d);
+    key.push_back(es);
+    key.push_back(op);
+    for (int k = 0; k < d; ++k) key.push_back(g.l[k]);
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(key);
+        if (it != g_plans.end()) { *plan = it->second; return true; }
+    }
+    int m[kFD];
+    if (!choose_m(g, es, op, m)) return false;
+    Plan p;
+    if (!build_plan_m(g, es, op, m, &p)) return false;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[key] = p;
+    *plan = p;
+    return true;
+}
+
+template <typename ST, bool FIX, int OP>
+int launch_closure(const Plan &pl, const std::vector<ClassPlan> &cls, const Geom &g, ST *u, cudaStream_t st)
+{
+    if (cls.empty()) return GBH_OK;
+    LaunchParams P{};
+    P.d = pl.d;
+    P.ncls = (int)cls.size();
+    P.N = g.N;
+    size_t smem_rows = 0, smem_wrows = 0, smem_vals = 0;
+    int64_t acc = 0;
+    double pts = 0.0;
+    for (int i = 0; i < P.ncls; ++i) {
+        P.cls[i] = cls[i].desc;
+        P.cls[i].grp_base = acc;
+        acc += cls[i].desc.groups;
+        smem_rows = std::max(smem_rows, (size_t)cls[i].desc.rows);
+        smem_wrows = std::max(smem_wrows, (size_t)cls[i].desc.wrows);
+        smem_vals = std::max(smem_vals, (size_t)cls[i].desc.V * sizeof(typename std::conditional<FIX, long long, ST>::type));
+        pts += (double)cls[i].desc.groups * cls[i].desc.W;
+    }
+    P.per_grid = acc;
+    P.total = acc * g.batch;
+    P.off_wg = (int)al16(smem_rows * 8);
+    P.off_ws = P.off_wg + (int)al16(smem_wrows * 8);
+    P.off_vals = P.off_ws + (int)al16(smem_wrows * 4);
+    const size_t smem = P.off_vals + smem_vals;
+    static int attr_done[2][2][2] = {};
+    int &flag = attr_done[sizeof(ST) == 8][FIX][OP == OP_D];
+    if (!flag) {
+        cudaFuncSetAttribute(k_closure<ST, FIX, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        flag = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure<ST, FIX, OP>, kThreads, smem);
+    if (per_sm < 1) return GBH_EUNSUPPORTED;
+    const int64_t grid = std::min<int64_t>(P.total, (int64_t)num_sms() * per_sm);
+    static const char *names[4] = {"fused_class0", "fused_class1", "fused_class2", "fused_class3+"};
+    const int csz = popc(cls[0].mask);
+    ProfScope ps(names[std::min(csz, 3)], st, 2.0 * sizeof(ST) * pts * g.batch);
+    k_closure<ST, FIX, OP><<<(unsigned)grid, kThreads, smem, st>>>(P, u);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+template <typename ST, int OP>
+int launch_lattice(const Plan &pl, const ClassPlan &cp, int k, const Geom &g, ST *u, cudaStream_t st)
+{
+    LatticeParams L{};
+    L.d = pl.d;
+    L.k = k;
+    L.lev = g.l[k] - pl.m[k];
+    L.pstride = ((int64_t)1 << pl.m[k]) * g.S[k];
+    int64_t poles = 1;
+    for (int j = 0; j < pl.d; ++j) {
+        L.S[j] = g.S[j];
+        L.m_pow[j] = (int64_t)1 << pl.m[j];
+        if (j == k) { L.cnt[j] = 1; L.kind[j] = 1; continue; }
+        if ((cp.mask >> j) & 1u) {
+            L.kind[j] = 1;
+            L.cnt[j] = ((int64_t)1 << (g.l[j] - pl.m[j])) + 1;
+        } else {
+            L.kind[j] = 0;
+            L.cnt[j] = ((int64_t)1 << (g.l[j] - pl.m[j])) * (L.m_pow[j] - 1);
+        }
+        poles *= L.cnt[j];
+    }
+    L.poles = poles;
+    L.total = poles * g.batch;
+    L.N = g.N;
+    const int64_t want = (L.total + kThreads - 1) / kThreads;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+    ProfScope ps("fused_lattice", st, 2.0 * sizeof(ST) * (double)L.total * ((1 << L.lev) + 1));
+    k_lattice<ST, OP><<<(unsigned)grid, kThreads, 0, st>>>(L, u);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+template <typename ST, bool FIX, int OP>
+int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
+{
+    const int d = pl.d;
+    if (OP == OP_H) {
+        for (int c = 0; c <= d; ++c) {
+            if (int e = launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st)) return e;
+            for (const ClassPlan &cp : pl.by_size[c])
+                for (int i = 0; i < cp.npoint; ++i)
+                    if (int e = launch_lattice<ST, OP>(pl, cp, cp.point_dims[i], g, u, st)) return e;
+        }
+    } else {
+        for (int c = d; c >= 0; --c) {
+            for (const ClassPlan &cp : pl.by_size[c])
+                for (int i = 0; i < cp.npoint; ++i)
+                    if (int e = launch_lattice<ST, OP>(pl, cp, cp.point_dims[i], g, u, st)) return e;
+            if (int e = launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st)) return e;
+        }
+    }
+    return GBH_OK;
+}
+
+}  // namespace
+
+bool fused_supported(const Geom &g, int dtype, int op)
+{
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return false;
+    (void)dtype;
+    return g.d >= 2 && g.d <= kFD;       // one dimension is one pass already
+}
+
+bool fused_tiles(const Geom &g, int dtype, int op, int *m_out)
+{
+    if (!fused_supported(g, dtype, op)) return false;
+    Plan pl;
+    if (!build_plan(g, dtype == GBH_F64 ? 8 : 4, op, nullptr, &pl)) return false;
+    for (int k = 0; k < g.d; ++k) m_out[k] = pl.m[k];
+    return true;
+}
+
+int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt, cudaStream_t s)
+{
+    const int es = dtype == GBH_F64 ? 8 : 4;
+    Plan pl;
+    const int *m_req = opt ? opt->tile_exp : nullptr;
+    if (!build_plan(g, es, op, m_req, &pl)) return GBH_EUNSUPPORTED;
+    const int arith = opt ? opt->arith : 0;
+    if (dtype == GBH_F64) {
+        double *u = static_cast<double *>(data);
+        const bool fix = arith != 1;
+        if (op == OP_H) return fix ? run_plan<double, true, OP_H>(pl, g, u, s) : run_plan<double, false, OP_H>(pl, g, u, s);
+        return fix ? run_plan<double, true, OP_D>(pl, g, u, s) : run_plan<double, false, OP_D>(pl, g, u, s);
+    }
+    float *u = static_cast<float *>(data);
+    if (op == OP_H) return run_plan<float, false, OP_H>(pl, g, u, s);
+    return run_plan<float, false, OP_D>(pl, g, u, s);
 }
 
 }  // namespace gbh

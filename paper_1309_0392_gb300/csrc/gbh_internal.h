@@ -54,6 +54,9 @@ int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s
 int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,
                     cudaStream_t s);
 
+// Tile exponents the fused path would choose (false if unsupported).
+bool fused_tiles(const Geom &g, int dtype, int op, int *m_out);
+
 // True if the fused path supports this (geometry, dtype, op).
 bool fused_supported(const Geom &g, int dtype, int op);
 
