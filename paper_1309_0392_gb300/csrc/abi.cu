@@ -172,8 +172,7 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     }
     // planner's choice: the fused path when it takes the shape and the grid is
     // large enough to tile, else one sweep per dimension
-    int m[kMaxDim] = {0};
-    if (g.N >= 4096 && fused_tiles(g, dtype, op, m)) return fused_transform(data, g, dtype, op, opt, s);
+    if (g.N >= 4096 && fused_preferred(g, dtype, op)) return fused_transform(data, g, dtype, op, opt, s);
     return plain_transform(data, g, dtype, op, s);
 }
 

@@ -73,6 +73,7 @@ struct ClassDesc {
     int wrows;           // W / we[0]
     int g0;              // fixed point: bits of the input scale
     int doublings;       // fixed point: doubling passes (hierarchization)
+    int growth_bits;     // fixed point, inverse: bits the block stage may add
 };
 
 struct LaunchParams {
@@ -87,37 +88,57 @@ struct LaunchParams {
     ClassDesc cls[kMaxCls];
 };
 
-__host__ __device__ inline unsigned magic_of(int e) { return (unsigned)(0xFFFFFFFFu / (unsigned)e) + 1u; }
-__device__ __forceinline__ int udiv(int n, unsigned mag) { return (int)__umulhi((unsigned)n, mag); }
+// n / e for 0 <= n < 2^32 / e as __umulhi(n, ceil(2^32 / e)); e = 1 has no
+// 32-bit magic and is marked by 0.
+__host__ __device__ inline unsigned magic_of(int e) { return e == 1 ? 0u : (unsigned)(0xFFFFFFFFu / (unsigned)e) + 1u; }
+__device__ __forceinline__ int udiv(int n, unsigned mag) { return mag ? (int)__umulhi((unsigned)n, mag) : n; }
 
 // ---------------------------------------------------------------------------
 // fixed point <-> fp64
 // ---------------------------------------------------------------------------
 
 // v = sign * M * 2^{c - (emax - e)}, M the 53-bit significand: the input scaled
-// so that the largest magnitude of the closure sits just below 2^{g0}.
-__device__ __forceinline__ long long to_fixed(long long bits, int emax, int c)
+// so that the largest magnitude of the closure sits just below 2^{g0}
+// (c = g0 - 53).  Computed as (M << P) >> rs with P = max(c, 0) and
+// rs = emax - e + P - c >= 0; shifts past the significand give 0, so zeros and
+// subnormals (e = 0) become 0 whenever emax >= 64 (checked per closure).
+__device__ __forceinline__ long long to_fixed(long long bits, int emax, int P, int rbias)
 {
-    const int e = (int)((bits >> 52) & 0x7FF);
+    const int e = (int)((unsigned long long)bits >> 52) & 0x7FF;
+    const unsigned long long M = (((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << P;
+    int rs = emax - e + rbias;
+    rs = rs > 63 ? 63 : rs;
+    const long long v = (long long)(M >> rs);
+    return bits < 0 ? -v : v;
+}
+
+// v * 2^X rounded to fp64 once: the integer-to-fp64 conversion rounds, the
+// power of two is an exponent-field add.  Valid for every nonzero v when the
+// closure's exponent range is moderate (checked per closure).
+__device__ __forceinline__ double from_fixed(long long v, long long Xhi)
+{
+    const long long b = __double_as_longlong(__ll2double_rn(v));
+    return __longlong_as_double(v == 0 ? 0ll : b + Xhi);
+}
+
+// Out-of-range closures (all values below 2^-960 or near the fp64 maximum):
+// exact but slow conversions.
+__device__ __noinline__ long long to_fixed_slow(long long bits, int emax, int c)
+{
+    const int e = (int)((unsigned long long)bits >> 52) & 0x7FF;
+    if (e == 0) return 0;
     const unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     const int sh = c - (emax - e);
     long long v;
-    if (e == 0) v = 0;
-    else if (sh >= 0) v = (long long)(M << sh);
+    if (sh >= 0) v = (long long)(M << sh);
     else v = (-sh >= 63) ? 0 : (long long)(M >> (-sh));
     return bits < 0 ? -v : v;
 }
 
-// v * 2^X rounded to fp64 once (the integer-to-fp64 conversion rounds; the
-// power of two is exact unless the result leaves the normal range).
-__device__ __forceinline__ double from_fixed(long long v, int X)
+__device__ __noinline__ double from_fixed_slow(long long v, int X)
 {
     if (v == 0) return 0.0;
-    const double r = __ll2double_rn(v);
-    const long long b = __double_as_longlong(r);
-    const int ne = (int)((b >> 52) & 0x7FF) + X;
-    if (ne > 0 && ne < 2047) return __longlong_as_double(b + ((long long)X << 52));
-    return ldexp(r, X);
+    return ldexp(__ll2double_rn(v), X);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,11 +216,46 @@ __device__ __forceinline__ void pole_dispatch(V *s, int st, int e)
 // interior, or those with some other block coordinate on the block boundary.
 enum PoleSet { ALL = 0, INTERIOR = 1, FACE = 2 };
 
+template <typename V, int E, int PO>
+__device__ __forceinline__ unsigned long long pole_smem_or(V *s, int st)
+{
+    V v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) v[i] = s[i * st];
+    pole_regs<V, E, PO>(v);
+    unsigned long long o = 0ull;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        s[i * st] = v[i];
+        if constexpr (std::is_same<V, long long>::value) o |= (unsigned long long)(v[i] ^ (v[i] >> 63));
+    }
+    return o;
+}
+
 template <typename V, int PO>
-__device__ void pass_dim(V *vals, const ClassDesc &C, int d, int k, int set)
+__device__ __forceinline__ unsigned long long pole_dispatch_or(V *s, int st, int e)
+{
+    switch (e) {
+        case 3: return pole_smem_or<V, 3, PO>(s, st);
+        case 5: return pole_smem_or<V, 5, PO>(s, st);
+        case 9: return pole_smem_or<V, 9, PO>(s, st);
+        case 17: return pole_smem_or<V, 17, PO>(s, st);
+        case 33: return pole_smem_or<V, 33, PO>(s, st);
+        case 65:
+            if constexpr (max_extent(sizeof(V)) >= 65) return pole_smem_or<V, 65, PO>(s, st);
+            return 0ull;
+        default: return 0ull;
+    }
+}
+
+// Applies pole operation PO along closure dimension k to the poles of `set`;
+// returns the OR of the magnitudes written (fixed point; 0 otherwise).
+template <typename V, int PO>
+__device__ unsigned long long pass_dim(V *vals, const ClassDesc &C, int d, int k, int set)
 {
     const int ek = C.e[k];
     const int npoles = C.V / ek;
+    unsigned long long orv = 0ull;
     for (int p = threadIdx.x; p < npoles; p += blockDim.x) {
         int rem = p, off = 0;
         bool interior = true;
@@ -214,8 +270,10 @@ __device__ void pass_dim(V *vals, const ClassDesc &C, int d, int k, int set)
         }
         if (set == INTERIOR && !interior) continue;
         if (set == FACE && interior) continue;
-        pole_dispatch<V, PO>(vals + off, C.ss[k], ek);
+        if (set == ALL) pole_dispatch<V, PO>(vals + off, C.ss[k], ek);
+        else orv |= pole_dispatch_or<V, PO>(vals + off, C.ss[k], ek);
     }
+    return orv;
 }
 
 // ---------------------------------------------------------------------------
@@ -234,6 +292,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
     int *s_ws = reinterpret_cast<int *>(sm + P.off_ws);         // shared base of every write row
     V *vals = reinterpret_cast<V *>(sm + P.off_vals);
     __shared__ int s_emax;
+    __shared__ unsigned long long s_or;
     const int tid = threadIdx.x, T = blockDim.x;
     const int d = P.d;
 
@@ -279,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
             s_ws[r] = crow * C.e[0] + C.wlo[0];
             s_wg[r] = crow;       // closure row; global base filled below
         }
-        if (tid == 0) s_emax = 0;
+        if (tid == 0) { s_emax = 0; s_or = 0ull; }
         __syncthreads();
         for (int r = tid; r < C.wrows; r += T) s_wg[r] = rowg[s_wg[r]] + (int64_t)C.wlo[0] * C.gstride[0];
 
@@ -316,14 +375,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
             }
         }
         int X = 0;
+        bool fast = true;
         if constexpr (FIX) {
             emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
             if ((tid & 31) == 0) atomicMax(&s_emax, emax);
             __syncthreads();
             emax = s_emax;
             const int cshift = C.g0 - 53;
-            for (int e = tid; e < C.V; e += T) vals[e] = (V)to_fixed((long long)vals[e], emax, cshift);
             X = emax - 1075 - cshift - (OP == OP_H ? C.doublings : 0);
+            fast = emax >= 64 && emax <= 1900;
+            if (fast) {
+                const int P = cshift > 0 ? cshift : 0;
+                const int rbias = P - cshift;
+                for (int e = tid; e < C.V; e += T) vals[e] = (V)to_fixed((long long)vals[e], emax, P, rbias);
+            } else {
+                for (int e = tid; e < C.V; e += T) vals[e] = (V)to_fixed_slow((long long)vals[e], emax, cshift);
+            }
         }
         __syncthreads();
 
@@ -335,19 +402,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
                 __syncthreads();
             }
         } else {
-            // lattice dimensions: surpluses -> partial nodal values, interior poles only
+            // stage A.  Lattice dimensions: surpluses -> partial nodal values,
+            // interior poles only
+            unsigned long long orv = 0ull;
             for (int k = 0; k < d; ++k) {
                 if (C.lev[k] == 0 || C.mode[k] != LATTICE) continue;
-                pass_dim<V, FIX ? P_D_FIX : P_D_NAT>(vals, C, d, k, INTERIOR);
+                orv |= pass_dim<V, FIX ? P_D_FIX : P_D_NAT>(vals, C, d, k, INTERIOR);
                 __syncthreads();
             }
             // block faces hold final nodal values: hierarchize them in the
             // block dimensions, so the closure holds one consistent vector
             for (int k = 0; k < d; ++k) {
                 if (C.lev[k] == 0 || C.mode[k] != BLOCK) continue;
-                pass_dim<V, FIX ? P_H_HALF : P_H_NAT>(vals, C, d, k, FACE);
+                orv |= pass_dim<V, FIX ? P_H_HALF : P_H_NAT>(vals, C, d, k, FACE);
                 __syncthreads();
             }
+            if constexpr (FIX) {
+                // renormalise to the magnitude stage A reached, leaving room
+                // for the growth of the block stage
+                orv |= (1ull << C.g0) - 1ull;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
+                if ((tid & 31) == 0) atomicOr(&s_or, orv);
+                __syncthreads();
+                int shift = (64 - __clzll((long long)s_or)) + C.growth_bits - 62;
+                if (shift > 0) {
+                    for (int e = tid; e < C.V; e += T) vals[e] = vals[e] >> shift;
+                    X += shift;
+                    __syncthreads();
+                }
+            }
+            // stage B: the block dehierarchization on the whole closure
             for (int k = 0; k < d; ++k) {
                 if (C.lev[k] == 0 || C.mode[k] != BLOCK) continue;
                 pass_dim<V, FIX ? P_D_FIX : P_D_NAT>(vals, C, d, k, ALL);
@@ -359,14 +444,228 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
         {
             const int we0 = C.we[0];
             const int64_t gs0 = C.gstride[0];
+            const long long Xhi = (long long)X << 52;
             for (int e = tid; e < C.W; e += T) {
                 const int r = udiv(e, C.wmag[0]);
                 const int x = e - r * we0;
                 const V v = vals[s_ws[r] + x];
                 ST out;
-                if constexpr (FIX) out = (ST)from_fixed((long long)v, X);
+                if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v, Xhi) : (ST)from_fixed_slow((long long)v, X);
                 else out = (ST)v;
                 u[s_wg[r] + (int64_t)x * gs0] = out;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// interior class of a 3-D grid with a compile-time tile E0 x E1 x E2
+// ---------------------------------------------------------------------------
+//
+// The same computation as k_closure for the class of points interior to their
+// tile in every dimension, with the index arithmetic resolved at compile time:
+// the first pass converts rows to fixed point while it transforms them, the
+// last pass writes the tile's interior straight from registers.  Dehierarchize
+// runs in two fixed-point stages: the tile faces (final nodal values) are
+// hierarchized, the values are renormalised to the magnitude they actually
+// reached, then the block dehierarchization runs on the whole tile.
+
+struct Tile3Params {
+    int64_t S1, S2;          // grid strides of dimensions 1 and 2
+    int64_t nb0, nb1;        // tiles along dimensions 0 and 1
+    int64_t tiles;           // tiles per grid
+    int64_t total;           // tiles * batch
+    int64_t N;               // points per grid
+    int g0;                  // fixed point: input scale bits
+    int growth_bits;         // dehierarchize: bits the block stage may add
+};
+
+template <typename V>
+__device__ __forceinline__ unsigned long long mag_bits_or(V v)
+{
+    if constexpr (std::is_same<V, long long>::value) return (unsigned long long)(v ^ (v >> 63));
+    else return 0ull;
+}
+
+template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
+__global__ void __launch_bounds__(kThreads, 2) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
+{
+    using V = typename std::conditional<FIX, long long, ST>::type;
+    constexpr int NV = E0 * E1 * E2, R = E1 * E2, P1 = E0 * E2, P2 = E0 * E1;
+    constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
+    extern __shared__ __align__(16) unsigned char sm[];
+    V *vals = reinterpret_cast<V *>(sm);
+    __shared__ int s_emax;
+    __shared__ unsigned long long s_or;
+    const int tid = threadIdx.x;
+    constexpr int T = kThreads;
+
+    for (int64_t G = blockIdx.x; G < P.total; G += gridDim.x) {
+        const int64_t b = G / P.tiles;
+        int64_t t = G - b * P.tiles;
+        const int64_t bx = t % P.nb0;
+        t /= P.nb0;
+        const int64_t by = t % P.nb1, bz = t / P.nb1;
+        ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
+        if (tid == 0) { s_emax = 0; s_or = 0ull; }
+
+        // load the closed tile
+        int emax = 0;
+        {
+            constexpr int U = 8;
+#pragma unroll 1
+            for (int e0 = tid; e0 < NV; e0 += T * U) {
+                ST tmp[U];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int e = e0 + q * T;
+                    if (e < NV) {
+                        const int x = e % E0, r = e / E0;
+                        const int y = r % E1, z = r / E1;
+                        tmp[q] = ub[x + y * P.S1 + z * P.S2];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const int e = e0 + q * T;
+                    if (e < NV) {
+                        if constexpr (FIX) {
+                            const long long bits = __double_as_longlong((double)tmp[q]);
+                            const int ex = (int)((unsigned long long)bits >> 52) & 0x7FF;
+                            emax = ex > emax ? ex : emax;
+                            vals[e] = (V)bits;
+                        } else {
+                            vals[e] = (V)tmp[q];
+                        }
+                    }
+                }
+            }
+        }
+        int X = 0, P_ = 0, rbias = 0, cshift = 0;
+        bool fast = true;
+        if constexpr (FIX) {
+            emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+            if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+            __syncthreads();
+            emax = s_emax;
+            cshift = P.g0 - 53;
+            P_ = cshift > 0 ? cshift : 0;
+            rbias = P_ - cshift;
+            X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
+            fast = emax >= 64 && emax <= 1900;
+        } else {
+            __syncthreads();
+        }
+
+        unsigned long long orv = 0ull;
+        // dimension 0: convert, then hierarchize (all rows) or, for the
+        // inverse, hierarchize the face rows
+        for (int r = tid; r < R; r += T) {
+            V v[E0];
+#pragma unroll
+            for (int i = 0; i < E0; ++i) {
+                V w = vals[r * E0 + i];
+                if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
+                v[i] = w;
+            }
+            if constexpr (OP == OP_H) {
+                pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
+            } else {
+                const int y = r % E1, z = r / E1;
+                if (y == 0 || y == B1 || z == 0 || z == B2) {
+                    pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
+#pragma unroll
+                    for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
+        }
+        __syncthreads();
+        // dimension 1
+        for (int p = tid; p < P1; p += T) {
+            const int x = p % E0, z = p / E0;
+            V *s = vals + x + z * E0 * E1;
+            if constexpr (OP == OP_H) {
+                pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(s, E0);
+            } else if (x == 0 || x == B0 || z == 0 || z == B2) {
+                V v[E1];
+#pragma unroll
+                for (int i = 0; i < E1; ++i) v[i] = s[i * E0];
+                pole_regs<V, E1, FIX ? P_H_HALF : P_H_NAT>(v);
+#pragma unroll
+                for (int i = 0; i < E1; ++i) { s[i * E0] = v[i]; orv |= mag_bits_or(v[i]); }
+            }
+        }
+        __syncthreads();
+        if constexpr (OP == OP_D) {
+            // dimension 2 on the faces, then renormalise for the block stage
+            for (int p = tid; p < P2; p += T) {
+                const int x = p % E0, y = p / E0;
+                if (x == 0 || x == B0 || y == 0 || y == B1) {
+                    V *s = vals + x + y * E0;
+                    V v[E2];
+#pragma unroll
+                    for (int i = 0; i < E2; ++i) v[i] = s[i * E0 * E1];
+                    pole_regs<V, E2, FIX ? P_H_HALF : P_H_NAT>(v);
+#pragma unroll
+                    for (int i = 0; i < E2; ++i) { s[i * E0 * E1] = v[i]; orv |= mag_bits_or(v[i]); }
+                }
+            }
+            int shift = 0;
+            if constexpr (FIX) {
+                // interior values are still inputs: below 2^{g0}
+                orv |= (1ull << P.g0) - 1ull;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
+                if ((tid & 31) == 0) atomicOr(&s_or, orv);
+                __syncthreads();
+                const int bits = 64 - __clzll((long long)s_or);
+                shift = bits + P.growth_bits - 62;
+                shift = shift > 0 ? shift : 0;
+                X += shift;
+            } else {
+                __syncthreads();
+            }
+            for (int r = tid; r < R; r += T) {
+                V v[E0];
+#pragma unroll
+                for (int i = 0; i < E0; ++i) {
+                    V w = vals[r * E0 + i];
+                    if constexpr (FIX) w = w >> shift;
+                    v[i] = w;
+                }
+                pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
+#pragma unroll
+                for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
+            }
+            __syncthreads();
+            for (int p = tid; p < P1; p += T) {
+                const int x = p % E0, z = p / E0;
+                pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
+            }
+            __syncthreads();
+        }
+        // dimension 2, then write the interior
+        const long long Xhi = (long long)X << 52;
+        for (int p = tid; p < P2; p += T) {
+            const int x = p % E0, y = p / E0;
+            V *s = vals + x + y * E0;
+            V v[E2];
+#pragma unroll
+            for (int i = 0; i < E2; ++i) v[i] = s[i * E0 * E1];
+            if constexpr (OP == OP_H) pole_regs<V, E2, FIX ? P_H_DBL : P_H_NAT>(v);
+            else pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
+            if (x > 0 && x < B0 && y > 0 && y < B1) {
+                ST *o = ub + x + y * P.S1;
+#pragma unroll
+                for (int i = 1; i < E2 - 1; ++i) {
+                    ST out;
+                    if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
+                    else out = (ST)v[i];
+                    o[i * P.S2] = out;
+                }
             }
         }
         __syncthreads();
@@ -561,17 +860,26 @@ bool make_class(const Geom &g, const int *m, unsigned mask, int es, size_t cap, 
     c.wrows = c.W / c.we[0];
     c.groups = 1;
     for (int k = 0; k < d; ++k) c.groups *= c.ngrp[k];
-    // fixed-point headroom
+    // fixed-point headroom.  Hierarchization: each pass at most quadruples
+    // 2u - L - R.  Inverse, stage A: lattice dehierarchization of the
+    // interior (growth prod gD) and face hierarchization (2 per block
+    // dimension) touch disjoint points; stage B: block dehierarchization.
     int passes = 0;
-    double growth = 1.0;
+    double gA_lat = 1.0, gA_face = 1.0, gB = 1.0;
     for (int k = 0; k < d; ++k) {
         if (c.lev[k] == 0) continue;
         ++passes;
-        if (op == OP_D) growth *= (c.mode[k] == BLOCK ? 2.0 : 1.0) * dehier_growth(c.lev[k]);
+        if (c.mode[k] == BLOCK) { gA_face *= 2.0; gB *= dehier_growth(c.lev[k]); }
+        else gA_lat *= dehier_growth(c.lev[k]);
     }
     c.doublings = passes;
-    if (op == OP_H) c.g0 = 61 - 2 * passes;
-    else c.g0 = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
+    if (op == OP_H) {
+        c.g0 = 61 - 2 * passes;
+        c.growth_bits = 0;
+    } else {
+        c.g0 = 61 - (int)std::ceil(std::log2(std::max(gA_lat, gA_face)) + 1e-9);
+        c.growth_bits = (int)std::ceil(std::log2(gB) + 1e-9);
+    }
     cp.npoint = 0;
     for (int k = 0; k < d; ++k)
         if (c.mode[k] == POINT) cp.point_dims[cp.npoint++] = k;
@@ -613,6 +921,8 @@ double estimate_bytes(const Geom &g, const int *m, int es, int op, size_t cap, b
 std::mutex g_plan_mu;
 std::map<std::vector<int>, Plan> g_plans;
 
+bool tile3_shape_ok(int es, int E0, int E1, int E2);
+
 // Tile exponents minimising the estimated DRAM bytes, subject to: every
 // dimension of level >= 1 has a block interior (m_k >= 1); every lattice
 // extent 2^{l_k - m_k} + 1 and block extent 2^{m_k} + 1 fits a register pole;
@@ -631,13 +941,22 @@ bool choose_m(const Geom &g, int es, int op, int *m_out)
         hi[k] = std::min(g.l[k], emax_lev);
         if (lo[k] > hi[k]) return false;
     }
+    // 3-D grids: prefer the tiles that have a compile-time interior kernel
+    bool want_t3 = false;
+    if (d == 3) {
+        for (int a = lo[0]; a <= hi[0]; ++a)
+            for (int b = lo[1]; b <= hi[1]; ++b)
+                for (int c = lo[2]; c <= hi[2]; ++c)
+                    want_t3 |= tile3_shape_ok(es, (1 << a) + 1, (1 << b) + 1, (1 << c) + 1);
+    }
     for (int k = 0; k < d; ++k) m[k] = lo[k];
     double best = 1e300;
     bool found = false;
     for (;;) {
         int64_t vol = 1;
         for (int k = 0; k < d; ++k) vol *= (int64_t)(1 << m[k]) + 1;
-        if ((size_t)vol * es <= cap / 2) {
+        const bool t3ok = !want_t3 || tile3_shape_ok(es, (1 << m[0]) + 1, (1 << m[1]) + 1, (1 << m[2]) + 1);
+        if (t3ok && (size_t)vol * es <= cap / 2) {
             bool ok;
             const double b = estimate_bytes(g, m, es, op, cap, &ok);
             if (ok && b < best) {
@@ -753,6 +1072,82 @@ int launch_closure(const Plan &pl, const std::vector<ClassPlan> &cls, const Geom
     return check_launch();
 }
 
+// Compile-time tiles of the interior-class kernel (E0, E1, E2).
+template <typename ST, bool FIX, int OP>
+struct Tile3Table;
+
+#define GBH_TILE3_LIST(X) X(33, 17, 17) X(17, 17, 17) X(33, 17, 9) X(65, 17, 17) X(65, 17, 9)
+
+bool tile3_shape_ok(int es, int E0, int E1, int E2)
+{
+    if (E0 > max_extent(es) || E1 > max_extent(es) || E2 > max_extent(es)) return false;
+#define GBH_TILE3_CMP(a, b, c) if (E0 == a && E1 == b && E2 == c) return true;
+    GBH_TILE3_LIST(GBH_TILE3_CMP)
+#undef GBH_TILE3_CMP
+    return false;
+}
+
+template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
+int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes)
+{
+    using V = typename std::conditional<FIX, long long, ST>::type;
+    constexpr size_t smem = (size_t)E0 * E1 * E2 * sizeof(V);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tile3<ST, FIX, OP, E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile3<ST, FIX, OP, E0, E1, E2>, kThreads, smem);
+    if (per_sm < 1) return GBH_EUNSUPPORTED;
+    const int64_t grid = std::min<int64_t>(P.total, (int64_t)num_sms() * per_sm);
+    ProfScope ps("fused_class0", st, alg_bytes);
+    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)grid, kThreads, smem, st>>>(P, u);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+// Launches the compile-time interior kernel for a 3-D class-0 closure;
+// returns 1 if no compile-time tile matches (the generic kernel then runs).
+template <typename ST, bool FIX, int OP>
+int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cudaStream_t st)
+{
+    const ClassDesc &c = cp.desc;
+    const int E0 = c.e[0], E1 = c.e[1], E2 = c.e[2];
+    if (pl.d != 3 || cp.mask != 0 || !tile3_shape_ok((int)sizeof(ST), E0, E1, E2)) return 1;
+    Tile3Params P{};
+    P.S1 = g.S[1];
+    P.S2 = g.S[2];
+    P.nb0 = c.ngrp[0];
+    P.nb1 = c.ngrp[1];
+    P.tiles = c.ngrp[0] * c.ngrp[1] * c.ngrp[2];
+    P.total = P.tiles * g.batch;
+    P.N = g.N;
+    if (OP == OP_H) {
+        P.g0 = 61 - 2 * 3;
+        P.growth_bits = 0;
+    } else {
+        P.g0 = 61 - 3;
+        double gr = 1.0;
+        for (int k = 0; k < 3; ++k) gr *= dehier_growth(c.lev[k]);
+        P.growth_bits = (int)std::ceil(std::log2(gr) + 1e-9);
+    }
+    const double bytes = 2.0 * sizeof(ST) * (double)P.total * c.W;
+#define GBH_TILE3_CALL(a, b, cc) \
+    if (E0 == a && E1 == b && E2 == cc) return launch_tile3_shape<ST, FIX, OP, a, b, cc>(P, u, st, bytes);
+    if constexpr (sizeof(ST) == 8) {
+        // fp64 keeps register poles to 33 points
+        if (E0 == 33 && E1 == 17 && E2 == 17) return launch_tile3_shape<ST, FIX, OP, 33, 17, 17>(P, u, st, bytes);
+        if (E0 == 17 && E1 == 17 && E2 == 17) return launch_tile3_shape<ST, FIX, OP, 17, 17, 17>(P, u, st, bytes);
+        if (E0 == 33 && E1 == 17 && E2 == 9) return launch_tile3_shape<ST, FIX, OP, 33, 17, 9>(P, u, st, bytes);
+    } else {
+        GBH_TILE3_LIST(GBH_TILE3_CALL)
+    }
+#undef GBH_TILE3_CALL
+    return 1;
+}
+
 template <typename ST, int OP>
 int launch_lattice(const Plan &pl, const ClassPlan &cp, int k, const Geom &g, ST *u, cudaStream_t st)
 {
@@ -791,9 +1186,16 @@ template <typename ST, bool FIX, int OP>
 int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
 {
     const int d = pl.d;
+    auto closure = [&](int c) -> int {
+        if (c == 0 && pl.by_size[0].size() == 1) {
+            const int r = launch_tile3<ST, FIX, OP>(pl, pl.by_size[0][0], g, u, st);
+            if (r != 1) return r;
+        }
+        return launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st);
+    };
     if (OP == OP_H) {
         for (int c = 0; c <= d; ++c) {
-            if (int e = launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st)) return e;
+            if (int e = closure(c)) return e;
             for (const ClassPlan &cp : pl.by_size[c])
                 for (int i = 0; i < cp.npoint; ++i)
                     if (int e = launch_lattice<ST, OP>(pl, cp, cp.point_dims[i], g, u, st)) return e;
@@ -803,7 +1205,7 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
             for (const ClassPlan &cp : pl.by_size[c])
                 for (int i = 0; i < cp.npoint; ++i)
                     if (int e = launch_lattice<ST, OP>(pl, cp, cp.point_dims[i], g, u, st)) return e;
-            if (int e = launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st)) return e;
+            if (int e = closure(c)) return e;
         }
     }
     return GBH_OK;
@@ -816,6 +1218,20 @@ bool fused_supported(const Geom &g, int dtype, int op)
     if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return false;
     (void)dtype;
     return g.d >= 2 && g.d <= kFD;       // one dimension is one pass already
+}
+
+bool fused_preferred(const Geom &g, int dtype, int op)
+{
+    if (!fused_supported(g, dtype, op)) return false;
+    const int es = dtype == GBH_F64 ? 8 : 4;
+    Plan pl;
+    if (!build_plan(g, es, op, nullptr, &pl)) return false;
+    bool ok = false;
+    const double fused = estimate_bytes(g, pl.m, es, op, 200 * 1024, &ok);
+    int passes = 0;
+    for (int k = 0; k < g.d; ++k) passes += g.l[k] > 0;
+    const double plain = 2.0 * es * (double)g.N * passes;
+    return ok && fused < 0.7 * plain;
 }
 
 bool fused_tiles(const Geom &g, int dtype, int op, int *m_out)

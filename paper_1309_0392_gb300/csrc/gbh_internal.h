@@ -57,6 +57,10 @@ int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_opti
 // Tile exponents the fused path would choose (false if unsupported).
 bool fused_tiles(const Geom &g, int dtype, int op, int *m_out);
 
+// True if the planner would rather run the fused path than the plain one
+// (estimated DRAM bytes well below one sweep per dimension).
+bool fused_preferred(const Geom &g, int dtype, int op);
+
 // True if the fused path supports this (geometry, dtype, op).
 bool fused_supported(const Geom &g, int dtype, int op);
 

@@ -27,7 +27,9 @@ def run(u, levels, op, dtype=torch.float64, **kw):
 
 
 def rel_err(a, b, u):
-    return np.abs(a - b).max() / max(np.abs(u).max(), 1e-300)
+    """max |a - b| relative to max|u| over the nodal side: the input of a
+    hierarchization, the output of a dehierarchization (max of both)."""
+    return np.abs(a - b).max() / max(np.abs(u).max(), np.abs(b).max(), 1e-300)
 
 
 # (levels, tile exponents); None = the planner's choice
