@@ -488,96 +488,128 @@ __device__ __forceinline__ unsigned long long mag_bits_or(V v)
     else return 0ull;
 }
 
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int kTile3Threads = 576;
+
+// One CTA per SM, persistent over the tiles; two tile buffers: while tile i is
+// transformed, tile i+1 streams in with cp.async.  Element offsets inside a
+// tile are the same for every tile and live in a shared-memory table.
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
-__global__ void __launch_bounds__(kThreads, 2) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
+__global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
 {
     using V = typename std::conditional<FIX, long long, ST>::type;
+    static_assert(sizeof(V) == sizeof(ST), "in-place conversion needs equal sizes");
+    constexpr int T = kTile3Threads;
     constexpr int NV = E0 * E1 * E2, R = E1 * E2, P1 = E0 * E2, P2 = E0 * E1;
     constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
+    constexpr int PER = (NV + T - 1) / T;
     extern __shared__ __align__(16) unsigned char sm[];
-    V *vals = reinterpret_cast<V *>(sm);
-    __shared__ int s_emax;
-    __shared__ unsigned long long s_or;
+    V *bufs = reinterpret_cast<V *>(sm);
+    int *offs = reinterpret_cast<int *>(sm + 2 * (size_t)NV * sizeof(V));
+    __shared__ int s_emax[2];
+    __shared__ unsigned long long s_or[2];
     const int tid = threadIdx.x;
-    constexpr int T = kThreads;
 
-    for (int64_t G = blockIdx.x; G < P.total; G += gridDim.x) {
+    for (int e = tid; e < NV; e += T) {
+        const int x = e % E0, r = e / E0;
+        offs[e] = (int)(x + (r % E1) * P.S1 + (r / E1) * P.S2);
+    }
+    __syncthreads();
+
+    auto tile_base = [&](int64_t G) -> ST * {
         const int64_t b = G / P.tiles;
         int64_t t = G - b * P.tiles;
         const int64_t bx = t % P.nb0;
         t /= P.nb0;
         const int64_t by = t % P.nb1, bz = t / P.nb1;
-        ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
-        if (tid == 0) { s_emax = 0; s_or = 0ull; }
-
-        // load the closed tile
-        int emax = 0;
-        {
-            constexpr int U = 8;
-#pragma unroll 1
-            for (int e0 = tid; e0 < NV; e0 += T * U) {
-                ST tmp[U];
+        return u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
+    };
+    auto issue = [&](int64_t G, V *dst) {
+        const ST *src = tile_base(G);
 #pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const int e = e0 + q * T;
-                    if (e < NV) {
-                        const int x = e % E0, r = e / E0;
-                        const int y = r % E1, z = r / E1;
-                        tmp[q] = ub[x + y * P.S1 + z * P.S2];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const int e = e0 + q * T;
-                    if (e < NV) {
-                        if constexpr (FIX) {
-                            const long long bits = __double_as_longlong((double)tmp[q]);
-                            const int ex = (int)((unsigned long long)bits >> 52) & 0x7FF;
-                            emax = ex > emax ? ex : emax;
-                            vals[e] = (V)bits;
-                        } else {
-                            vals[e] = (V)tmp[q];
-                        }
-                    }
-                }
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * T;
+            if (k < PER - 1 || e < NV) {
+                if constexpr (sizeof(ST) == 8) cp_async8(dst + e, src + offs[e]);
+                else cp_async4(dst + e, src + offs[e]);
             }
         }
-        int X = 0, P_ = 0, rbias = 0, cshift = 0;
+        cp_async_commit();
+    };
+
+    int cur = 0;
+    if (blockIdx.x < P.total) issue(blockIdx.x, bufs);
+    for (int64_t G = blockIdx.x; G < P.total; G += gridDim.x, cur ^= 1) {
+        if (tid == 0) { s_emax[cur] = 0; s_or[cur] = 0ull; }
+        cp_async_wait_all();
+        __syncthreads();
+        if (G + gridDim.x < P.total) issue(G + gridDim.x, bufs + (size_t)(cur ^ 1) * NV);
+        V *vals = bufs + (size_t)cur * NV;
+        ST *__restrict__ ub = tile_base(G);
+
+        int X = 0;
         bool fast = true;
         if constexpr (FIX) {
+            // largest binary exponent of the tile, then everything to fixed point
+            long long raw[PER];
+            int emax = 0;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                const int e = tid + k * T;
+                raw[k] = (k < PER - 1 || e < NV) ? (long long)vals[e] : 0ll;
+                const int ex = (int)((unsigned long long)raw[k] >> 52) & 0x7FF;
+                emax = ex > emax ? ex : emax;
+            }
             emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
-            if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+            if ((tid & 31) == 0) atomicMax(&s_emax[cur], emax);
             __syncthreads();
-            emax = s_emax;
-            cshift = P.g0 - 53;
-            P_ = cshift > 0 ? cshift : 0;
-            rbias = P_ - cshift;
+            emax = s_emax[cur];
+            const int cshift = P.g0 - 53;
+            const int P_ = cshift > 0 ? cshift : 0, rbias = P_ - cshift;
             X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
             fast = emax >= 64 && emax <= 1900;
-        } else {
+            if (fast) {
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = tid + k * T;
+                    if (k < PER - 1 || e < NV) vals[e] = to_fixed(raw[k], emax, P_, rbias);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = tid + k * T;
+                    if (k < PER - 1 || e < NV) vals[e] = to_fixed_slow(raw[k], emax, cshift);
+                }
+            }
             __syncthreads();
         }
 
         unsigned long long orv = 0ull;
-        // dimension 0: convert, then hierarchize (all rows) or, for the
-        // inverse, hierarchize the face rows
+        // dimension 0: hierarchize every row, or (inverse) the face rows
         for (int r = tid; r < R; r += T) {
+            const int y = r % E1, z = r / E1;
+            if (OP == OP_D && !(y == 0 || y == B1 || z == 0 || z == B2)) continue;
             V v[E0];
 #pragma unroll
-            for (int i = 0; i < E0; ++i) {
-                V w = vals[r * E0 + i];
-                if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
-                v[i] = w;
-            }
+            for (int i = 0; i < E0; ++i) v[i] = vals[r * E0 + i];
             if constexpr (OP == OP_H) {
                 pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
             } else {
-                const int y = r % E1, z = r / E1;
-                if (y == 0 || y == B1 || z == 0 || z == B2) {
-                    pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
+                pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
 #pragma unroll
-                    for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
-                }
+                for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
             }
 #pragma unroll
             for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
@@ -586,43 +618,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile3(const __grid_constant__ T
         // dimension 1
         for (int p = tid; p < P1; p += T) {
             const int x = p % E0, z = p / E0;
-            V *s = vals + x + z * E0 * E1;
+            V *sp = vals + x + z * E0 * E1;
             if constexpr (OP == OP_H) {
-                pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(s, E0);
+                pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
             } else if (x == 0 || x == B0 || z == 0 || z == B2) {
-                V v[E1];
-#pragma unroll
-                for (int i = 0; i < E1; ++i) v[i] = s[i * E0];
-                pole_regs<V, E1, FIX ? P_H_HALF : P_H_NAT>(v);
-#pragma unroll
-                for (int i = 0; i < E1; ++i) { s[i * E0] = v[i]; orv |= mag_bits_or(v[i]); }
+                orv |= pole_smem_or<V, E1, FIX ? P_H_HALF : P_H_NAT>(sp, E0);
             }
         }
         __syncthreads();
         if constexpr (OP == OP_D) {
-            // dimension 2 on the faces, then renormalise for the block stage
+            // dimension 2 on the faces, renormalise, block stage on dims 0, 1
             for (int p = tid; p < P2; p += T) {
                 const int x = p % E0, y = p / E0;
-                if (x == 0 || x == B0 || y == 0 || y == B1) {
-                    V *s = vals + x + y * E0;
-                    V v[E2];
-#pragma unroll
-                    for (int i = 0; i < E2; ++i) v[i] = s[i * E0 * E1];
-                    pole_regs<V, E2, FIX ? P_H_HALF : P_H_NAT>(v);
-#pragma unroll
-                    for (int i = 0; i < E2; ++i) { s[i * E0 * E1] = v[i]; orv |= mag_bits_or(v[i]); }
-                }
+                if (x == 0 || x == B0 || y == 0 || y == B1)
+                    orv |= pole_smem_or<V, E2, FIX ? P_H_HALF : P_H_NAT>(vals + x + y * E0, E0 * E1);
             }
             int shift = 0;
             if constexpr (FIX) {
-                // interior values are still inputs: below 2^{g0}
                 orv |= (1ull << P.g0) - 1ull;
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
-                if ((tid & 31) == 0) atomicOr(&s_or, orv);
+                if ((tid & 31) == 0) atomicOr(&s_or[cur], orv);
                 __syncthreads();
-                const int bits = 64 - __clzll((long long)s_or);
-                shift = bits + P.growth_bits - 62;
+                shift = (64 - __clzll((long long)s_or[cur])) + P.growth_bits - 62;
                 shift = shift > 0 ? shift : 0;
                 X += shift;
             } else {
@@ -647,14 +665,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile3(const __grid_constant__ T
             }
             __syncthreads();
         }
-        // dimension 2, then write the interior
+        // dimension 2, then the tile interior goes straight to global memory
         const long long Xhi = (long long)X << 52;
         for (int p = tid; p < P2; p += T) {
             const int x = p % E0, y = p / E0;
-            V *s = vals + x + y * E0;
+            V *sp = vals + x + y * E0;
             V v[E2];
 #pragma unroll
-            for (int i = 0; i < E2; ++i) v[i] = s[i * E0 * E1];
+            for (int i = 0; i < E2; ++i) v[i] = sp[i * E0 * E1];
             if constexpr (OP == OP_H) pole_regs<V, E2, FIX ? P_H_DBL : P_H_NAT>(v);
             else pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
             if (x > 0 && x < B0 && y > 0 && y < B1) {
@@ -668,8 +686,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile3(const __grid_constant__ T
                 }
             }
         }
-        __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -1090,19 +1108,19 @@ bool tile3_shape_ok(int es, int E0, int E1, int E2)
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
 int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes)
 {
-    using V = typename std::conditional<FIX, long long, ST>::type;
-    constexpr size_t smem = (size_t)E0 * E1 * E2 * sizeof(V);
+    constexpr size_t NV = (size_t)E0 * E1 * E2;
+    constexpr size_t smem = 2 * NV * sizeof(ST) + NV * sizeof(int);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tile3<ST, FIX, OP, E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile3<ST, FIX, OP, E0, E1, E2>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile3<ST, FIX, OP, E0, E1, E2>, kTile3Threads, smem);
     if (per_sm < 1) return GBH_EUNSUPPORTED;
     const int64_t grid = std::min<int64_t>(P.total, (int64_t)num_sms() * per_sm);
     ProfScope ps("fused_class0", st, alg_bytes);
-    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)grid, kThreads, smem, st>>>(P, u);
+    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)grid, kTile3Threads, smem, st>>>(P, u);
     ps.done();
     count_launches(1);
     return check_launch();
@@ -1116,6 +1134,10 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
     const ClassDesc &c = cp.desc;
     const int E0 = c.e[0], E1 = c.e[1], E2 = c.e[2];
     if (pl.d != 3 || cp.mask != 0 || !tile3_shape_ok((int)sizeof(ST), E0, E1, E2)) return 1;
+    // element offsets inside a tile are kept as int32
+    if ((int64_t)(E0 - 1) + (E1 - 1) * g.S[1] + (E2 - 1) * g.S[2] >= INT32_MAX) return 1;
+    // two tile buffers and the offset table must fit shared memory
+    if ((size_t)E0 * E1 * E2 * (2 * sizeof(ST) + sizeof(int)) > 226 * 1024) return 1;
     Tile3Params P{};
     P.S1 = g.S[1];
     P.S2 = g.S[2];
