@@ -501,112 +501,94 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-constexpr int kTile3Threads = 576;
+constexpr int kTile3Group = 320;                  // threads of one tile pipeline
+constexpr int kTile3Groups = 2;                   // pipelines per CTA (one CTA per SM)
+constexpr int kTile3Threads = kTile3Group * kTile3Groups;
 
-// One CTA per SM, persistent over the tiles; two tile buffers: while tile i is
-// transformed, tile i+1 streams in with cp.async.  Element offsets inside a
-// tile are the same for every tile and live in a shared-memory table.
+__device__ __forceinline__ void group_sync(int id)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(kTile3Group) : "memory");
+}
+
+// One CTA per SM holding two independent tile pipelines (warp groups with
+// their own named barrier and tile buffer), persistent over the tiles, so the
+// load, integer and conversion phases of the two pipelines overlap.  Element
+// offsets inside a tile are the same for every tile: one shared table.
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
 __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
 {
     using V = typename std::conditional<FIX, long long, ST>::type;
     static_assert(sizeof(V) == sizeof(ST), "in-place conversion needs equal sizes");
-    constexpr int T = kTile3Threads;
+    constexpr int T = kTile3Group;
     constexpr int NV = E0 * E1 * E2, R = E1 * E2, P1 = E0 * E2, P2 = E0 * E1;
     constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
-    constexpr int PER = (NV + T - 1) / T;
     extern __shared__ __align__(16) unsigned char sm[];
-    V *bufs = reinterpret_cast<V *>(sm);
-    int *offs = reinterpret_cast<int *>(sm + 2 * (size_t)NV * sizeof(V));
-    __shared__ int s_emax[2];
-    __shared__ unsigned long long s_or[2];
-    const int tid = threadIdx.x;
+    int *offs = reinterpret_cast<int *>(sm);
+    constexpr size_t offs_bytes = ((size_t)NV * sizeof(int) + 15) / 16 * 16;
+    __shared__ int s_emax[kTile3Groups];
+    __shared__ unsigned long long s_or[kTile3Groups];
 
-    for (int e = tid; e < NV; e += T) {
+    for (int e = threadIdx.x; e < NV; e += kTile3Threads) {
         const int x = e % E0, r = e / E0;
         offs[e] = (int)(x + (r % E1) * P.S1 + (r / E1) * P.S2);
     }
     __syncthreads();
 
-    auto tile_base = [&](int64_t G) -> ST * {
+    const int grp = threadIdx.x / T, tid = threadIdx.x - grp * T, bar = 1 + grp;
+    V *vals = reinterpret_cast<V *>(sm + offs_bytes + (size_t)grp * NV * sizeof(V));
+    const int64_t first = (int64_t)blockIdx.x * kTile3Groups + grp, step = (int64_t)gridDim.x * kTile3Groups;
+
+    for (int64_t G = first; G < P.total; G += step) {
         const int64_t b = G / P.tiles;
         int64_t t = G - b * P.tiles;
         const int64_t bx = t % P.nb0;
         t /= P.nb0;
         const int64_t by = t % P.nb1, bz = t / P.nb1;
-        return u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
-    };
-    auto issue = [&](int64_t G, V *dst) {
-        const ST *src = tile_base(G);
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * T;
-            if (k < PER - 1 || e < NV) {
-                if constexpr (sizeof(ST) == 8) cp_async8(dst + e, src + offs[e]);
-                else cp_async4(dst + e, src + offs[e]);
-            }
+        ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
+        if (tid == 0) { s_emax[grp] = 0; s_or[grp] = 0ull; }
+        for (int e = tid; e < NV; e += T) {
+            if constexpr (sizeof(ST) == 8) cp_async8(vals + e, ub + offs[e]);
+            else cp_async4(vals + e, ub + offs[e]);
         }
         cp_async_commit();
-    };
-
-    int cur = 0;
-    if (blockIdx.x < P.total) issue(blockIdx.x, bufs);
-    for (int64_t G = blockIdx.x; G < P.total; G += gridDim.x, cur ^= 1) {
-        if (tid == 0) { s_emax[cur] = 0; s_or[cur] = 0ull; }
         cp_async_wait_all();
-        __syncthreads();
-        if (G + gridDim.x < P.total) issue(G + gridDim.x, bufs + (size_t)(cur ^ 1) * NV);
-        V *vals = bufs + (size_t)cur * NV;
-        ST *__restrict__ ub = tile_base(G);
+        group_sync(bar);
 
-        int X = 0;
+        int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
         bool fast = true;
         if constexpr (FIX) {
-            // largest binary exponent of the tile, then everything to fixed point
-            long long raw[PER];
-            int emax = 0;
-#pragma unroll
-            for (int k = 0; k < PER; ++k) {
-                const int e = tid + k * T;
-                raw[k] = (k < PER - 1 || e < NV) ? (long long)vals[e] : 0ll;
-                const int ex = (int)((unsigned long long)raw[k] >> 52) & 0x7FF;
+            // largest binary exponent of the tile (high words only)
+            const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
+            for (int e = tid; e < NV; e += T) {
+                const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
                 emax = ex > emax ? ex : emax;
             }
             emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
-            if ((tid & 31) == 0) atomicMax(&s_emax[cur], emax);
-            __syncthreads();
-            emax = s_emax[cur];
-            const int cshift = P.g0 - 53;
-            const int P_ = cshift > 0 ? cshift : 0, rbias = P_ - cshift;
+            if ((tid & 31) == 0) atomicMax(&s_emax[grp], emax);
+            group_sync(bar);
+            emax = s_emax[grp];
+            cshift = P.g0 - 53;
+            P_ = cshift > 0 ? cshift : 0;
+            rbias = P_ - cshift;
             X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
             fast = emax >= 64 && emax <= 1900;
-            if (fast) {
-#pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    const int e = tid + k * T;
-                    if (k < PER - 1 || e < NV) vals[e] = to_fixed(raw[k], emax, P_, rbias);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    const int e = tid + k * T;
-                    if (k < PER - 1 || e < NV) vals[e] = to_fixed_slow(raw[k], emax, cshift);
-                }
-            }
-            __syncthreads();
         }
 
         unsigned long long orv = 0ull;
-        // dimension 0: hierarchize every row, or (inverse) the face rows
+        // dimension 0: convert every row, hierarchize every row or (inverse)
+        // the face rows
         for (int r = tid; r < R; r += T) {
             const int y = r % E1, z = r / E1;
-            if (OP == OP_D && !(y == 0 || y == B1 || z == 0 || z == B2)) continue;
             V v[E0];
 #pragma unroll
-            for (int i = 0; i < E0; ++i) v[i] = vals[r * E0 + i];
+            for (int i = 0; i < E0; ++i) {
+                V w = vals[r * E0 + i];
+                if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
+                v[i] = w;
+            }
             if constexpr (OP == OP_H) {
                 pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
-            } else {
+            } else if (y == 0 || y == B1 || z == 0 || z == B2) {
                 pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
 #pragma unroll
                 for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
@@ -614,7 +596,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
 #pragma unroll
             for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
         }
-        __syncthreads();
+        group_sync(bar);
         // dimension 1
         for (int p = tid; p < P1; p += T) {
             const int x = p % E0, z = p / E0;
@@ -625,7 +607,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
                 orv |= pole_smem_or<V, E1, FIX ? P_H_HALF : P_H_NAT>(sp, E0);
             }
         }
-        __syncthreads();
+        group_sync(bar);
         if constexpr (OP == OP_D) {
             // dimension 2 on the faces, renormalise, block stage on dims 0, 1
             for (int p = tid; p < P2; p += T) {
@@ -638,13 +620,13 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
                 orv |= (1ull << P.g0) - 1ull;
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
-                if ((tid & 31) == 0) atomicOr(&s_or[cur], orv);
-                __syncthreads();
-                shift = (64 - __clzll((long long)s_or[cur])) + P.growth_bits - 62;
+                if ((tid & 31) == 0) atomicOr(&s_or[grp], orv);
+                group_sync(bar);
+                shift = (64 - __clzll((long long)s_or[grp])) + P.growth_bits - 62;
                 shift = shift > 0 ? shift : 0;
                 X += shift;
             } else {
-                __syncthreads();
+                group_sync(bar);
             }
             for (int r = tid; r < R; r += T) {
                 V v[E0];
@@ -658,12 +640,12 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
 #pragma unroll
                 for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
             }
-            __syncthreads();
+            group_sync(bar);
             for (int p = tid; p < P1; p += T) {
                 const int x = p % E0, z = p / E0;
                 pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
             }
-            __syncthreads();
+            group_sync(bar);
         }
         // dimension 2, then the tile interior goes straight to global memory
         const long long Xhi = (long long)X << 52;
@@ -686,8 +668,8 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
                 }
             }
         }
+        group_sync(bar);
     }
-    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -1109,7 +1091,7 @@ template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
 int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes)
 {
     constexpr size_t NV = (size_t)E0 * E1 * E2;
-    constexpr size_t smem = 2 * NV * sizeof(ST) + NV * sizeof(int);
+    constexpr size_t smem = (NV * sizeof(int) + 15) / 16 * 16 + kTile3Groups * NV * sizeof(ST);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tile3<ST, FIX, OP, E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1137,7 +1119,7 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
     // element offsets inside a tile are kept as int32
     if ((int64_t)(E0 - 1) + (E1 - 1) * g.S[1] + (E2 - 1) * g.S[2] >= INT32_MAX) return 1;
     // two tile buffers and the offset table must fit shared memory
-    if ((size_t)E0 * E1 * E2 * (2 * sizeof(ST) + sizeof(int)) > 226 * 1024) return 1;
+    if ((size_t)E0 * E1 * E2 * (kTile3Groups * sizeof(ST) + sizeof(int)) + 16 > 226 * 1024) return 1;
     Tile3Params P{};
     P.S1 = g.S[1];
     P.S2 = g.S[2];
