@@ -121,37 +121,6 @@ __device__ __forceinline__ double from_fixed(long long v, long long Xhi)
     return __longlong_as_double(v == 0 ? 0ll : b + Xhi);
 }
 
-// Same as to_fixed with a compile-time pre-shift PC = max(c, 0) and
-// emaxp = emax + PC - c.  Shifts of 32 or more take a (rare) slow branch.
-template <int PC>
-__device__ __forceinline__ long long to_fixed_c(long long bits, int emaxp)
-{
-    const unsigned hi = (unsigned)((unsigned long long)bits >> 32), lo = (unsigned)bits;
-    const int rs = emaxp - (int)((hi >> 20) & 0x7FFu);
-    const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;
-    unsigned wh = PC ? __funnelshift_l(lo, mh, PC) : mh;
-    unsigned wl = lo << PC;
-    unsigned rl, rh;
-    if (rs < 32) {
-        rl = __funnelshift_r(wl, wh, rs);
-        rh = wh >> rs;
-    } else {
-        rl = rs < 64 ? (wh >> (rs - 32)) : 0u;
-        rh = 0u;
-    }
-    const unsigned sgn = (unsigned)((int)hi >> 31);
-    const unsigned long long v = (((unsigned long long)(rh ^ sgn) << 32) | (rl ^ sgn)) - (unsigned long long)(long long)(int)sgn;
-    return (long long)v;
-}
-
-// from_fixed with the zero test on the high word only.
-__device__ __forceinline__ double from_fixed_c(long long v, int Xhi32)
-{
-    const double r = __ll2double_rn(v);
-    const int h = __double2hiint(r);
-    return __hiloint2double(h == 0 ? 0 : h + Xhi32, __double2loint(r));
-}
-
 // Out-of-range closures (all values below 2^-960 or near the fp64 maximum):
 // exact but slow conversions.
 __device__ __noinline__ long long to_fixed_slow(long long bits, int emax, int c)
@@ -532,11 +501,6 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// compile-time pre-shift of the fast conversion: c = g0 - 53 of the
-// interior kernel (hierarchize g0 = 55, dehierarchize g0 = 58)
-template <int OP>
-struct kT3Pre { static constexpr int v = OP == GBH_HIERARCHIZE ? 2 : 5; };
-
 constexpr int kTile3Group = 320;                  // threads of one tile pipeline
 constexpr int kTile3Groups = 2;                   // pipelines per CTA (one CTA per SM)
 constexpr int kTile3Threads = kTile3Group * kTile3Groups;
@@ -593,15 +557,12 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
         int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
         bool fast = true;
         if constexpr (FIX) {
-            // largest binary exponent of the tile (high words only, two
-            // elements per 16-byte load)
-            const uint4 *q = reinterpret_cast<const uint4 *>(vals);
-            for (int e = tid; e < NV / 2; e += T) {
-                const uint4 w = q[e];
-                const unsigned m = max(w.y & 0x7FF00000u, w.w & 0x7FF00000u);
-                emax = max(emax, (int)(m >> 20));
+            // largest binary exponent of the tile (high words only)
+            const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
+            for (int e = tid; e < NV; e += T) {
+                const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
+                emax = ex > emax ? ex : emax;
             }
-            if (tid == 0 && (NV & 1)) emax = max(emax, (int)((reinterpret_cast<const unsigned *>(vals)[2 * NV - 1] >> 20) & 0x7FF));
             emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
             if ((tid & 31) == 0) atomicMax(&s_emax[grp], emax);
             group_sync(bar);
@@ -610,7 +571,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
             P_ = cshift > 0 ? cshift : 0;
             rbias = P_ - cshift;
             X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
-            fast = emax >= 64 && emax <= 1900 && P_ == kT3Pre<OP>::v;
+            fast = emax >= 64 && emax <= 1900;
         }
 
         unsigned long long orv = 0ull;
@@ -622,7 +583,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
 #pragma unroll
             for (int i = 0; i < E0; ++i) {
                 V w = vals[r * E0 + i];
-                if constexpr (FIX) w = fast ? to_fixed_c<kT3Pre<OP>::v>((long long)w, emax + rbias) : to_fixed_slow((long long)w, emax, cshift);
+                if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
                 v[i] = w;
             }
             if constexpr (OP == OP_H) {
@@ -687,7 +648,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
             group_sync(bar);
         }
         // dimension 2, then the tile interior goes straight to global memory
-        const int Xhi32 = X << 20;
+        const long long Xhi = (long long)X << 52;
         for (int p = tid; p < P2; p += T) {
             const int x = p % E0, y = p / E0;
             V *sp = vals + x + y * E0;
@@ -701,7 +662,7 @@ __global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constan
 #pragma unroll
                 for (int i = 1; i < E2 - 1; ++i) {
                     ST out;
-                    if constexpr (FIX) out = fast ? (ST)from_fixed_c((long long)v[i], Xhi32) : (ST)from_fixed_slow((long long)v[i], X);
+                    if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
                     else out = (ST)v[i];
                     o[i * P.S2] = out;
                 }
