@@ -1,19 +1,873 @@
-// Combination-scheme plans (batched transform, gather): not built yet.
+// Combination-scheme plans (Sec. 2): every grid of a scheme transformed by one
+// persistent kernel driven by a device work queue, and the fp64 gather of the
+// hierarchical surpluses into the sparse grid.
+//
+// Work items.  Each grid runs through phases: an exponent scan (fp64 only),
+// then one sweep per dimension.  Items are (grid, phase, range of rows or
+// poles) and are handed out by an atomic ticket in a fixed order: grids are
+// grouped into waves that fit in L2 together, and within a wave the items run
+// phase-major, so phase k+1 of a grid mostly reads phase k's output from L2.
+// An item of phase p waits (bounded spin) until every item of phase p-1 of its
+// grid has finished; tickets are taken in order by resident CTAs, so every
+// dependency is already owned by a running CTA.
+//
+// Arithmetic.  fp32 grids compute in fp32.  fp64 grids compute in exact int64
+// fixed point held in place between phases (the same 8 bytes per point): the
+// scan finds the grid's largest binary exponent, the first sweep converts,
+// the last sweep converts back.  Hierarchization uses the doubling form
+// 2u - L - R, so it rounds only once, at the final conversion.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
 #include "gbh_internal.h"
 
-struct gbh_plan { int unused; };
+namespace gbh {
+namespace {
+
+constexpr int kPlanMaxD = 8;
+constexpr int kBThreads = 256;
+constexpr int kRowsSmemElems = 8192;          // staged elements per rows item
+constexpr int64_t kItemPoints = 16384;        // target points per item
+constexpr double kWaveBytes = 48.0 * 1024 * 1024;
+constexpr long long kSpinLimit = 1ll << 24;   // bounded waits (~ seconds)
+
+enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
+enum ItemKind { K_SCAN = 0, K_ROWS = 1, K_POLES = 2, K_LONG = 3 };
+
+struct GridInfo {
+    int l[kPlanMaxD];
+    int64_t S[kPlanMaxD];
+    int64_t N;
+    int first_dim;       // first and last dimension with a sweep (-1: none)
+    int last_dim;
+    int g0;              // fixed point: input scale bits (per op)
+    int g0_d;
+    int passes;          // dimensions with a sweep
+};
+
+struct Item {
+    int grid;
+    int phase;           // 0 = scan (fp64), 1 + k = sweep of dimension k
+    int kind;
+    int dim;
+    int64_t start;       // first row / pole / element
+    int64_t count;
+    int wait;            // phase that must be complete first (-1: none)
+    int pad;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// fp64 <-> fixed point (see fused.cu for the derivation): the grid's largest
+// magnitude sits just below 2^{g0}.
+__device__ __forceinline__ long long b_to_fixed(double x, int emax, int c)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    if (e == 0) return 0;
+    const unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = c - (emax - e);
+    long long v;
+    if (sh >= 0) v = (long long)(M << sh);
+    else v = (-sh >= 63) ? 0 : (long long)(M >> (-sh));
+    return bits < 0 ? -v : v;
+}
+
+__device__ __forceinline__ double b_from_fixed(long long v, int X)
+{
+    if (v == 0) return 0.0;
+    const double r = __ll2double_rn(v);
+    const long long b = __double_as_longlong(r);
+    const int ne = (int)((b >> 52) & 0x7FF) + X;
+    if (ne > 0 && ne < 2047) return __longlong_as_double(b + ((long long)X << 52));
+    return ldexp(r, X);
+}
+
+struct BatchParams {
+    const Item *items;
+    int nitems;
+    const GridInfo *grids;
+    void *const *ptrs;
+    int *done;           // [ngrids * kPhases]
+    const int *need;     // items per (grid, phase)
+    int *emax;           // per grid
+    unsigned *ticket;
+    int *status;
+    int op;
+};
+constexpr int kPhases = 1 + kPlanMaxD;
+
+// value access for the three storage states of an fp64 grid: the first sweep
+// reads fp64 and converts, the last converts back, the others read int64.
+template <typename ST, int OP>
+struct Acc {
+    ST *p;
+    int emax, c, X;
+    bool first, last;
+    __device__ __forceinline__ long long rd(int64_t i) const
+    {
+        if constexpr (sizeof(ST) == 8) {
+            const long long raw = __ldcg(reinterpret_cast<const long long *>(p) + i);
+            return first ? b_to_fixed(__longlong_as_double(raw), emax, c) : raw;
+        } else {
+            return 0;
+        }
+    }
+    __device__ __forceinline__ void wr(int64_t i, long long v) const
+    {
+        if constexpr (sizeof(ST) == 8) {
+            long long o = last ? __double_as_longlong(b_from_fixed(v, X)) : v;
+            __stcg(reinterpret_cast<long long *>(p) + i, o);
+        }
+    }
+};
+
+template <int OP>
+__device__ __forceinline__ long long fx_op(long long v, long long L, long long R)
+{
+    if (OP == OP_H) return (v + v) - L - R;
+    return v + ((L + R) >> 1);
+}
+template <int OP, typename F>
+__device__ __forceinline__ F fl_op(F v, F L, F R)
+{
+    if (OP == OP_H) return v - F(0.5) * (L + R);
+    return v + F(0.5) * (L + R);
+}
+
+template <typename ST, int OP>
+__global__ void __launch_bounds__(kBThreads) k_batched(const BatchParams P)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    using V = typename std::conditional<sizeof(ST) == 8, long long, ST>::type;
+    V *sv = reinterpret_cast<V *>(sm);
+
+    for (;;) {
+        if (tid == 0) {
+            s_item = (int)atomicAdd(P.ticket, 1u);
+            s_abort = 0;
+            if (s_item < P.nitems) {
+                const Item it = P.items[s_item];
+                if (it.wait >= 0) {
+                    const int *cnt = P.done + it.grid * kPhases + it.wait;
+                    const int want = P.need[it.grid * kPhases + it.wait];
+                    long long spins = 0;
+                    while (ld_acquire(cnt) < want) {
+                        if (++spins > kSpinLimit) { atomicExch(P.status, GBH_ETIMEOUT); s_abort = 1; break; }
+                        __nanosleep(64);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int idx = s_item;
+        if (idx >= P.nitems || s_abort || ld_acquire(P.status) != 0) return;
+        const Item it = P.items[idx];
+        const GridInfo &gi = P.grids[it.grid];
+        ST *base = reinterpret_cast<ST *>(P.ptrs[it.grid]);
+
+        if (it.kind == K_SCAN) {
+            int em = 0;
+            const long long *b = reinterpret_cast<const long long *>(base);
+            for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
+                const int e = (int)((__ldcg(b + i) >> 52) & 0x7FF);
+                em = e > em ? e : em;
+            }
+            em = __reduce_max_sync(0xFFFFFFFFu, (unsigned)em);
+            if ((tid & 31) == 0 && em > 0) atomicMax(P.emax + it.grid, em);
+        } else {
+            const int k = it.dim, l = gi.l[k];
+            const int64_t n = ((int64_t)1 << l) + 1, S = gi.S[k], last_i = (int64_t)1 << l;
+            Acc<ST, OP> A;
+            A.p = base;
+            A.first = (k == gi.first_dim);
+            A.last = (k == gi.last_dim);
+            if constexpr (sizeof(ST) == 8) {
+                A.emax = ld_acquire(P.emax + it.grid);
+                const int g0 = OP == OP_H ? gi.g0 : gi.g0_d;
+                A.c = g0 - 53;
+                A.X = A.emax - 1075 - A.c - (OP == OP_H ? gi.passes : 0);
+            }
+            if (it.kind == K_ROWS) {
+                // dimension 0: `count` whole rows staged in shared memory
+                const int64_t e0 = it.start * n;
+                const int cnt = (int)(it.count * n);
+                for (int e = tid; e < cnt; e += blockDim.x) {
+                    if constexpr (sizeof(ST) == 8) sv[e] = A.rd(e0 + e);
+                    else sv[e] = __ldcg(base + e0 + e);
+                }
+                __syncthreads();
+                const int rows = (int)it.count;
+                if (OP == OP_H) {
+                    for (int lev = l; lev >= 1; --lev) {
+                        const int s = 1 << (l - lev), per = 1 << (lev - 1);
+                        for (int q = tid; q < rows * per; q += blockDim.x) {
+                            const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                            V *row = sv + r * n;
+                            if constexpr (sizeof(ST) == 8) row[i] = fx_op<OP>(row[i], row[i - s], row[i + s]);
+                            else row[i] = fl_op<OP>(row[i], row[i - s], row[i + s]);
+                        }
+                        __syncthreads();
+                    }
+                    if constexpr (sizeof(ST) == 8) {
+                        for (int r = tid; r < rows; r += blockDim.x) {
+                            sv[r * n] += sv[r * n];
+                            sv[r * n + last_i] += sv[r * n + last_i];
+                        }
+                        __syncthreads();
+                    }
+                } else {
+                    for (int lev = 1; lev <= l; ++lev) {
+                        const int s = 1 << (l - lev), per = 1 << (lev - 1);
+                        for (int q = tid; q < rows * per; q += blockDim.x) {
+                            const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                            V *row = sv + r * n;
+                            if constexpr (sizeof(ST) == 8) row[i] = fx_op<OP>(row[i], row[i - s], row[i + s]);
+                            else row[i] = fl_op<OP>(row[i], row[i - s], row[i + s]);
+                        }
+                        __syncthreads();
+                    }
+                }
+                for (int e = tid; e < cnt; e += blockDim.x) {
+                    if constexpr (sizeof(ST) == 8) A.wr(e0 + e, sv[e]);
+                    else __stcg(base + e0 + e, sv[e]);
+                }
+            } else if (it.kind == K_POLES) {
+                // one thread per pole, level by level in place (L2-resident)
+                for (int64_t t = it.start + tid; t < it.start + it.count; t += blockDim.x) {
+                    const int64_t o = t / S, j = t - o * S;
+                    const int64_t pb = o * S * n + j;
+                    if constexpr (sizeof(ST) == 8) {
+                        if (A.first)
+                            for (int64_t i = 0; i <= last_i; ++i) __stcg(reinterpret_cast<long long *>(base) + pb + i * S, A.rd(pb + i * S));
+                        Acc<ST, OP> B = A;
+                        B.first = false;
+                        B.last = false;
+                        if (OP == OP_H) {
+                            for (int lev = l; lev >= 1; --lev) {
+                                const int64_t s = (int64_t)1 << (l - lev);
+                                for (int64_t i = s; i < last_i; i += 2 * s)
+                                    B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
+                            }
+                            B.wr(pb, B.rd(pb) * 2);
+                            B.wr(pb + last_i * S, B.rd(pb + last_i * S) * 2);
+                        } else {
+                            for (int lev = 1; lev <= l; ++lev) {
+                                const int64_t s = (int64_t)1 << (l - lev);
+                                for (int64_t i = s; i < last_i; i += 2 * s)
+                                    B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
+                            }
+                        }
+                        if (A.last)
+                            for (int64_t i = 0; i <= last_i; ++i) A.wr(pb + i * S, B.rd(pb + i * S));
+                    } else {
+                        ST *pp = base + pb;
+                        if (OP == OP_H) {
+                            for (int lev = l; lev >= 1; --lev) {
+                                const int64_t s = (int64_t)1 << (l - lev);
+                                for (int64_t i = s; i < last_i; i += 2 * s)
+                                    __stcg(pp + i * S, fl_op<OP>(__ldcg(pp + i * S), __ldcg(pp + (i - s) * S), __ldcg(pp + (i + s) * S)));
+                            }
+                        } else {
+                            for (int lev = 1; lev <= l; ++lev) {
+                                const int64_t s = (int64_t)1 << (l - lev);
+                                for (int64_t i = s; i < last_i; i += 2 * s)
+                                    __stcg(pp + i * S, fl_op<OP>(__ldcg(pp + i * S), __ldcg(pp + (i - s) * S), __ldcg(pp + (i + s) * S)));
+                            }
+                        }
+                    }
+                }
+            } else {
+                // K_LONG: `count` long poles; the CTA sweeps them level by level
+                const int64_t npole = it.count;
+                auto pbase = [&](int64_t t) { const int64_t tt = it.start + t, o = tt / S; return o * S * n + (tt - o * S); };
+                if constexpr (sizeof(ST) == 8) {
+                    if (A.first) {
+                        for (int64_t w = tid; w < npole * n; w += blockDim.x) {
+                            const int64_t t = w % npole, i = w / npole;
+                            const int64_t a = pbase(t) + i * S;
+                            __stcg(reinterpret_cast<long long *>(base) + a, A.rd(a));
+                        }
+                        __syncthreads();
+                    }
+                }
+                Acc<ST, OP> B = A;
+                B.first = false;
+                B.last = false;
+                auto step = [&](int lev) {
+                    const int64_t s = (int64_t)1 << (l - lev), per = (int64_t)1 << (lev - 1);
+                    for (int64_t w = tid; w < npole * per; w += blockDim.x) {
+                        const int64_t t = w % npole, q = w / npole;
+                        const int64_t i = (2 * q + 1) * s, pb = pbase(t);
+                        if constexpr (sizeof(ST) == 8)
+                            B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
+                        else
+                            __stcg(base + pb + i * S, fl_op<OP>(__ldcg(base + pb + i * S), __ldcg(base + pb + (i - s) * S),
+                                                                __ldcg(base + pb + (i + s) * S)));
+                    }
+                    __syncthreads();
+                };
+                if (OP == OP_H) for (int lev = l; lev >= 1; --lev) step(lev);
+                else for (int lev = 1; lev <= l; ++lev) step(lev);
+                if constexpr (sizeof(ST) == 8) {
+                    if (OP == OP_H) {
+                        for (int64_t t = tid; t < npole; t += blockDim.x) {
+                            const int64_t pb = pbase(t);
+                            B.wr(pb, B.rd(pb) * 2);
+                            B.wr(pb + last_i * S, B.rd(pb + last_i * S) * 2);
+                        }
+                        __syncthreads();
+                    }
+                    if (A.last) {
+                        for (int64_t w = tid; w < npole * n; w += blockDim.x) {
+                            const int64_t t = w % npole, i = w / npole;
+                            const int64_t a = pbase(t) + i * S;
+                            A.wr(a, B.rd(a));
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(P.done + it.grid * kPhases + it.phase, 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// gather into the sparse grid
+// ---------------------------------------------------------------------------
+
+struct GatherParams {
+    int d;
+    int nsub;
+    const int64_t *sub_off;     // [nsub + 1] first sparse point of every subspace
+    const int *sub_j;           // [nsub * d] subspace levels
+    const int *list_off;        // [nsub + 1]
+    const int *list;            // grids containing each subspace, enumeration order
+    const GridInfo *grids;
+    void *const *ptrs;
+    const double *coeffs;
+    double *sparse;
+    int64_t total;
+    int fp64;
+};
+
+__global__ void __launch_bounds__(256) k_gather(const GatherParams P)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = P.nsub - 1;          // last subspace with sub_off <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.sub_off[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const int sb = lo;
+        int64_t pos = p - P.sub_off[sb];
+        int j[kPlanMaxD];
+        int64_t ps[kPlanMaxD];
+        for (int k = 0; k < P.d; ++k) {
+            j[k] = P.sub_j[sb * P.d + k];
+            const int64_t w = j[k] == 0 ? 2 : ((int64_t)1 << (j[k] - 1));
+            ps[k] = pos % w;
+            pos /= w;
+        }
+        double acc = 0.0;
+        for (int q = P.list_off[sb]; q < P.list_off[sb + 1]; ++q) {
+            const int g = P.list[q];
+            const GridInfo &gi = P.grids[g];
+            int64_t f = 0;
+            for (int k = 0; k < P.d; ++k) {
+                const int l = gi.l[k];
+                const int64_t i = j[k] == 0 ? ps[k] << l : (2 * ps[k] + 1) << (l - j[k]);
+                f += i * gi.S[k];
+            }
+            const double a = P.fp64 ? __ldg(reinterpret_cast<const double *>(P.ptrs[g]) + f)
+                                    : (double)__ldg(reinterpret_cast<const float *>(P.ptrs[g]) + f);
+            acc = __dadd_rn(acc, __dmul_rn(P.coeffs[g], a));
+        }
+        P.sparse[p] = acc;
+    }
+}
+
+double dgrowth(int lev)
+{
+    const int n = (1 << lev) + 1;
+    double best = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double s = 1.0;
+        for (int j = 1; j <= lev; ++j) {
+            const int st = 1 << (lev - j);
+            const int a = (i / (2 * st)) * (2 * st) + st;
+            if (a >= n - 1) continue;
+            const double w = 1.0 - std::fabs((double)(i - a)) / (double)st;
+            if (w > 0) s += w;
+        }
+        best = std::max(best, s);
+    }
+    return best;
+}
+
+}  // namespace
+}  // namespace gbh
+
+using namespace gbh;
+
+struct gbh_plan {
+    int d = 0, dtype = 0, n = -1, ngrids = 0;
+    std::vector<int32_t> levels;       // [G][d]
+    std::vector<double> coeffs;
+    std::vector<GridInfo> info;
+    std::vector<Item> items;
+    std::vector<int> need;             // [G][kPhases]
+    int64_t total_points = 0, sparse_points = 0;
+    // device
+    GridInfo *d_info = nullptr;
+    Item *d_items = nullptr;
+    int *d_need = nullptr;
+    void **d_ptrs = nullptr;
+    double *d_coeffs = nullptr;
+    unsigned char *d_scratch = nullptr;   // ticket | status | emax[G] | done[G][kPhases]
+    size_t scratch_bytes = 0;
+    int64_t *d_sub_off = nullptr;
+    int *d_sub_j = nullptr, *d_list_off = nullptr, *d_list = nullptr;
+    int nsub = 0;
+    void **h_ptrs = nullptr;          // pinned staging for bind
+    bool bound = false;
+    int dev = 0;
+};
+
+namespace {
+
+void free_plan(gbh_plan *p)
+{
+    if (!p) return;
+    cudaFree(p->d_info);
+    cudaFree(p->d_items);
+    cudaFree(p->d_need);
+    cudaFree(p->d_ptrs);
+    cudaFree(p->d_coeffs);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_sub_off);
+    cudaFree(p->d_sub_j);
+    cudaFree(p->d_list_off);
+    cudaFree(p->d_list);
+    if (p->h_ptrs) cudaFreeHost(p->h_ptrs);
+    delete p;
+}
+
+template <typename T>
+int upload(T **dst, const std::vector<T> &src)
+{
+    const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+    if (cudaMalloc(reinterpret_cast<void **>(dst), bytes) != cudaSuccess) return GBH_ENOMEM;
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return GBH_ECUDA;
+    return GBH_OK;
+}
+
+// Work items of one grid for phase p, appended to `out`.
+void grid_items(const GridInfo &gi, int g, int d, int es, int phase, std::vector<Item> &out, int &count)
+{
+    count = 0;
+    if (phase == 0) {
+        for (int64_t s = 0; s < gi.N; s += kItemPoints * 4) {
+            out.push_back(Item{g, 0, K_SCAN, 0, s, std::min<int64_t>(kItemPoints * 4, gi.N - s), -1, 0});
+            ++count;
+        }
+        return;
+    }
+    const int k = phase - 1;
+    if (k >= d || gi.l[k] == 0) return;
+    const int64_t n = ((int64_t)1 << gi.l[k]) + 1;
+    const int64_t poles = gi.N / n;
+    if (k == 0 && n <= kRowsSmemElems) {
+        const int64_t rpi = std::max<int64_t>(1, std::min<int64_t>(kRowsSmemElems / n, std::max<int64_t>(1, kItemPoints / n)));
+        for (int64_t s = 0; s < poles; s += rpi) {
+            out.push_back(Item{g, phase, K_ROWS, 0, s, std::min(rpi, poles - s), -1, 0});
+            ++count;
+        }
+        return;
+    }
+    (void)es;
+    // long poles with few of them: one CTA sweeps a group level by level
+    const bool longp = gi.l[k] > 5 && (poles < 4 * kBThreads || k == 0);
+    if (longp) {
+        const int64_t ppi = std::max<int64_t>(1, kItemPoints * 4 / n);
+        for (int64_t s = 0; s < poles; s += ppi) {
+            out.push_back(Item{g, phase, K_LONG, k, s, std::min(ppi, poles - s), -1, 0});
+            ++count;
+        }
+        return;
+    }
+    const int64_t ppi = std::max<int64_t>(kBThreads, kItemPoints / n);
+    for (int64_t s = 0; s < poles; s += ppi) {
+        out.push_back(Item{g, phase, K_POLES, k, s, std::min(ppi, poles - s), -1, 0});
+        ++count;
+    }
+}
+
+int build_items(gbh_plan *p)
+{
+    const int es = p->dtype == GBH_F64 ? 8 : 4;
+    p->need.assign((size_t)p->ngrids * kPhases, 0);
+    // waves of grids that fit in L2 together; phase-major inside a wave
+    std::vector<int> order(p->ngrids);
+    for (int g = 0; g < p->ngrids; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->info[a].N > p->info[b].N; });
+    size_t w0 = 0;
+    while (w0 < order.size()) {
+        size_t w1 = w0;
+        double bytes = 0.0;
+        while (w1 < order.size() && (w1 == w0 || bytes + (double)p->info[order[w1]].N * es <= kWaveBytes)) {
+            bytes += (double)p->info[order[w1]].N * es;
+            ++w1;
+        }
+        std::vector<int> prev(w1 - w0, -1);          // last phase with items, per grid
+        for (int ph = (p->dtype == GBH_F64 ? 0 : 1); ph < kPhases; ++ph)
+            for (size_t w = w0; w < w1; ++w) {
+                const int g = order[w];
+                if (p->info[g].first_dim < 0) continue;
+                int cnt = 0;
+                const size_t first = p->items.size();
+                grid_items(p->info[g], g, p->d, es, ph, p->items, cnt);
+                for (size_t i = first; i < p->items.size(); ++i) p->items[i].wait = prev[w - w0];
+                p->need[(size_t)g * kPhases + ph] = cnt;
+                if (cnt > 0) prev[w - w0] = ph;
+            }
+        w0 = w1;
+    }
+    return GBH_OK;
+}
+
+int finish_plan(gbh_plan *p)
+{
+    const int d = p->d;
+    p->info.resize(p->ngrids);
+    p->total_points = 0;
+    for (int g = 0; g < p->ngrids; ++g) {
+        GridInfo &gi = p->info[g];
+        std::memset(&gi, 0, sizeof(gi));
+        int64_t N = 1;
+        gi.first_dim = gi.last_dim = -1;
+        int passes = 0;
+        double growth = 1.0;
+        for (int k = 0; k < d; ++k) {
+            const int l = p->levels[(size_t)g * d + k];
+            if (l < 0 || l > 30) return GBH_ERANGE;
+            gi.l[k] = l;
+            gi.S[k] = N;
+            const int64_t nk = ((int64_t)1 << l) + 1;
+            if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
+            N *= nk;
+            if (l > 0) {
+                if (gi.first_dim < 0) gi.first_dim = k;
+                gi.last_dim = k;
+                ++passes;
+                growth *= dgrowth(std::min(l, 16));
+            }
+        }
+        gi.N = N;
+        gi.passes = passes;
+        gi.g0 = 61 - 2 * passes;
+        gi.g0_d = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
+        p->total_points += N;
+    }
+    if (int e = build_items(p)) return e;
+    if (int e = upload(&p->d_info, p->info)) return e;
+    if (int e = upload(&p->d_items, p->items)) return e;
+    if (int e = upload(&p->d_need, p->need)) return e;
+    if (int e = upload(&p->d_coeffs, p->coeffs)) return e;
+    if (cudaMalloc(reinterpret_cast<void **>(&p->d_ptrs), sizeof(void *) * p->ngrids) != cudaSuccess) return GBH_ENOMEM;
+    p->scratch_bytes = 64 + sizeof(int) * (size_t)p->ngrids * (1 + kPhases);
+    if (cudaMalloc(reinterpret_cast<void **>(&p->d_scratch), p->scratch_bytes) != cudaSuccess) return GBH_ENOMEM;
+    if (cudaMemset(p->d_scratch, 0, p->scratch_bytes) != cudaSuccess) return GBH_ECUDA;
+    if (cudaMallocHost(reinterpret_cast<void **>(&p->h_ptrs), sizeof(void *) * p->ngrids) != cudaSuccess) return GBH_ENOMEM;
+    cudaGetDevice(&p->dev);
+    return GBH_OK;
+}
+
+// sparse-grid subspaces of the scheme (d, n): lexicographic j, j_0 most significant
+int build_sparse(gbh_plan *p)
+{
+    const int d = p->d, n = p->n;
+    std::vector<int64_t> off;
+    std::vector<int> js, loff, list;
+    std::vector<int> j(d, 0);
+    int64_t acc = 0;
+    for (;;) {
+        int t = 0;
+        for (int k = 0; k < d; ++k) t += std::max(j[k], 1);
+        if (t <= n + d - 1) {
+            off.push_back(acc);
+            int64_t sz = 1;
+            for (int k = 0; k < d; ++k) sz *= (j[k] == 0) ? 2 : ((int64_t)1 << (j[k] - 1));
+            acc += sz;
+            for (int k = 0; k < d; ++k) js.push_back(j[k]);
+            loff.push_back((int)list.size());
+            for (int g = 0; g < p->ngrids; ++g) {
+                bool in = true;
+                for (int k = 0; k < d; ++k) in &= j[k] <= p->levels[(size_t)g * d + k];
+                if (in) list.push_back(g);
+            }
+        }
+        int k = d - 1;                             // j_{d-1} fastest
+        while (k >= 0 && ++j[k] > n) { j[k] = 0; --k; }
+        if (k < 0) break;
+    }
+    off.push_back(acc);
+    loff.push_back((int)list.size());
+    p->nsub = (int)js.size() / d;
+    p->sparse_points = acc;
+    if (int e = upload(&p->d_sub_off, off)) return e;
+    if (int e = upload(&p->d_sub_j, js)) return e;
+    if (int e = upload(&p->d_list_off, loff)) return e;
+    if (int e = upload(&p->d_list, list)) return e;
+    return GBH_OK;
+}
+
+// Appends every l in N_{>=1}^d with |l|_1 = s in lexicographic order (l_0
+// most significant): an odometer over l_0..l_{d-2}, l_{d-1} takes the rest.
+void add_compositions(gbh_plan *p, int s, double c)
+{
+    const int d = p->d;
+    std::vector<int> l(d, 1);
+    for (;;) {
+        int head = 0;
+        for (int k = 0; k < d - 1; ++k) head += l[k];
+        if (s - head >= 1) {
+            for (int k = 0; k < d - 1; ++k) p->levels.push_back(l[k]);
+            p->levels.push_back(s - head);
+            p->coeffs.push_back(c);
+        }
+        if (d == 1) break;
+        int k = d - 2;
+        while (k >= 0) {
+            ++l[k];
+            int h = 0;
+            for (int m = 0; m <= k; ++m) h += l[m];
+            if (h + (d - 1 - k) <= s) break;        // the tail still gets >= 1 each
+            l[k] = 1;
+            --k;
+        }
+        if (k < 0) break;
+    }
+}
+
+double binom(int n, int k)
+{
+    if (k < 0 || k > n) return 0.0;
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+}  // namespace
 
 extern "C" {
-int gbh_plan_create_scheme(int, int, int, gbh_plan **) { return GBH_EUNSUPPORTED; }
-int gbh_plan_create(int, int, const int32_t *, int, gbh_plan **) { return GBH_EUNSUPPORTED; }
-int gbh_plan_destroy(gbh_plan *) { return GBH_OK; }
-int gbh_plan_num_grids(const gbh_plan *, int *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_grid_levels(const gbh_plan *, int, int32_t *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_coeffs(const gbh_plan *, double *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_sparse_points(const gbh_plan *, int64_t *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_total_points(const gbh_plan *, int64_t *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_bind(gbh_plan *, void *const *, void *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_execute(gbh_plan *, int, void *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_gather(gbh_plan *, double *, void *) { return GBH_EUNSUPPORTED; }
-int gbh_plan_status(gbh_plan *, void *) { return GBH_EUNSUPPORTED; }
+
+int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out)
+{
+    if (!out) return GBH_EINVAL;
+    *out = nullptr;
+    if (d < 1 || d > kPlanMaxD || n < 1) return GBH_EINVAL;
+    if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
+    if (n + d - 1 > 30 + d - 1) return GBH_ERANGE;
+    gbh_plan *p = new (std::nothrow) gbh_plan();
+    if (!p) return GBH_ENOMEM;
+    p->d = d;
+    p->dtype = dtype;
+    p->n = n;
+    // every l with l_k >= 1 and |l|_1 = n + d - 1 - q; q ascending, then
+    // lexicographic order with l_0 most significant
+    for (int q = 0; q < d; ++q) {
+        const int s = n + d - 1 - q;
+        if (s < d) continue;
+        const double c = ((q & 1) ? -1.0 : 1.0) * binom(d - 1, q);
+        add_compositions(p, s, c);
+    }
+    p->ngrids = (int)p->coeffs.size();
+    int e = finish_plan(p);
+    if (!e) e = build_sparse(p);
+    if (e) { free_plan(p); return e; }
+    *out = p;
+    return GBH_OK;
 }
+
+int gbh_plan_create(int n_grids, int d, const int32_t *levels, int dtype, gbh_plan **out)
+{
+    if (!out) return GBH_EINVAL;
+    *out = nullptr;
+    if (n_grids < 1 || d < 1 || d > kPlanMaxD || !levels) return GBH_EINVAL;
+    if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
+    gbh_plan *p = new (std::nothrow) gbh_plan();
+    if (!p) return GBH_ENOMEM;
+    p->d = d;
+    p->dtype = dtype;
+    p->ngrids = n_grids;
+    p->levels.assign(levels, levels + (size_t)n_grids * d);
+    p->coeffs.assign(n_grids, 1.0);
+    if (int e = finish_plan(p)) { free_plan(p); return e; }
+    *out = p;
+    return GBH_OK;
+}
+
+int gbh_plan_destroy(gbh_plan *plan)
+{
+    if (!plan) return GBH_EINVAL;
+    free_plan(plan);
+    return GBH_OK;
+}
+
+int gbh_plan_num_grids(const gbh_plan *plan, int *out)
+{
+    if (!plan || !out) return GBH_EINVAL;
+    *out = plan->ngrids;
+    return GBH_OK;
+}
+
+int gbh_plan_grid_levels(const gbh_plan *plan, int g, int32_t *levels_out)
+{
+    if (!plan || !levels_out || g < 0 || g >= plan->ngrids) return GBH_EINVAL;
+    for (int k = 0; k < plan->d; ++k) levels_out[k] = plan->levels[(size_t)g * plan->d + k];
+    return GBH_OK;
+}
+
+int gbh_plan_coeffs(const gbh_plan *plan, double *coeffs_out)
+{
+    if (!plan || !coeffs_out) return GBH_EINVAL;
+    std::memcpy(coeffs_out, plan->coeffs.data(), sizeof(double) * plan->ngrids);
+    return GBH_OK;
+}
+
+int gbh_plan_sparse_points(const gbh_plan *plan, int64_t *out)
+{
+    if (!plan || !out) return GBH_EINVAL;
+    if (plan->n < 0) return GBH_EUNSUPPORTED;
+    *out = plan->sparse_points;
+    return GBH_OK;
+}
+
+int gbh_plan_total_points(const gbh_plan *plan, int64_t *out)
+{
+    if (!plan || !out) return GBH_EINVAL;
+    *out = plan->total_points;
+    return GBH_OK;
+}
+
+int gbh_plan_bind(gbh_plan *plan, void *const *grid_ptrs, void *stream)
+{
+    if (!plan || !grid_ptrs) return GBH_EINVAL;
+    const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
+    for (int g = 0; g < plan->ngrids; ++g) {
+        if (!grid_ptrs[g]) return GBH_EINVAL;
+        if (reinterpret_cast<uintptr_t>(grid_ptrs[g]) % es) return GBH_EALIGN;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the staging buffer may still feed an earlier copy
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
+    std::memcpy(plan->h_ptrs, grid_ptrs, sizeof(void *) * plan->ngrids);
+    if (cudaMemcpyAsync(plan->d_ptrs, plan->h_ptrs, sizeof(void *) * plan->ngrids, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return GBH_ECUDA;
+    plan->bound = true;
+    return GBH_OK;
+}
+
+int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
+{
+    if (!plan) return GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return op == GBH_ADJOINT ? GBH_EUNSUPPORTED : GBH_EINVAL;
+    if (!plan->bound) return GBH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // queue, status and counters restart with every execution
+    if (cudaMemsetAsync(plan->d_scratch, 0, plan->scratch_bytes, s) != cudaSuccess) return GBH_ECUDA;
+    BatchParams P{};
+    P.items = plan->d_items;
+    P.nitems = (int)plan->items.size();
+    P.grids = plan->d_info;
+    P.ptrs = plan->d_ptrs;
+    P.ticket = reinterpret_cast<unsigned *>(plan->d_scratch);
+    P.status = reinterpret_cast<int *>(plan->d_scratch + 32);
+    P.emax = reinterpret_cast<int *>(plan->d_scratch + 64);
+    P.done = P.emax + plan->ngrids;
+    P.need = plan->d_need;
+    P.op = op;
+    const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
+    const size_t smem = kRowsSmemElems * es;
+    auto launch = [&](auto kern) -> int {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem);
+        if (per_sm < 1) return GBH_EUNSUPPORTED;
+        const int grid = std::max(1, std::min(num_sms() * per_sm, P.nitems));
+        ProfScope ps("batched", s, 2.0 * es * (double)plan->total_points);
+        kern<<<grid, kBThreads, smem, s>>>(P);
+        ps.done();
+        count_launches(1);
+        return check_launch();
+    };
+    if (plan->dtype == GBH_F64)
+        return op == GBH_HIERARCHIZE ? launch(k_batched<double, OP_H>) : launch(k_batched<double, OP_D>);
+    return op == GBH_HIERARCHIZE ? launch(k_batched<float, OP_H>) : launch(k_batched<float, OP_D>);
+}
+
+int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
+{
+    if (!plan || !sparse) return GBH_EINVAL;
+    if (plan->n < 0) return GBH_EUNSUPPORTED;
+    if (!plan->bound) return GBH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(sparse) % 8) return GBH_EALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GatherParams G{};
+    G.d = plan->d;
+    G.nsub = plan->nsub;
+    G.sub_off = plan->d_sub_off;
+    G.sub_j = plan->d_sub_j;
+    G.list_off = plan->d_list_off;
+    G.list = plan->d_list;
+    G.grids = plan->d_info;
+    G.ptrs = plan->d_ptrs;
+    G.coeffs = plan->d_coeffs;
+    G.sparse = sparse;
+    G.total = plan->sparse_points;
+    G.fp64 = plan->dtype == GBH_F64;
+    const int64_t want = (G.total + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+    ProfScope ps("gather", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * G.total);
+    k_gather<<<grid, 256, 0, s>>>(G);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+int gbh_plan_status(gbh_plan *plan, void *stream)
+{
+    if (!plan) return GBH_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = 0;
+    if (cudaMemcpyAsync(&st, plan->d_scratch + 32, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GBH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
+    if (st != 0) {
+        const int zero = 0;
+        cudaMemcpy(plan->d_scratch + 32, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+"""GPU parity of combination-scheme plans: the batched persistent transform of
+every grid of a scheme and the fp64 gather into the sparse grid (Sec. 2),
+against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_0392_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+gbh = pytest.importorskip("paper_1309_0392_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b, u):
+    return np.abs(a - b).max() / max(np.abs(u).max(), np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("d,n", [(1, 5), (2, 5), (3, 4), (4, 4), (4, 14), (5, 3)])
+def test_scheme_matches_oracle(d, n):
+    plan = gbh.Plan.scheme(d, n)
+    lv, c = oracle.scheme(d, n)
+    assert plan.num_grids == len(lv)
+    assert np.array_equal(plan.levels(), lv)
+    assert np.array_equal(plan.coeffs(), c)
+    assert plan.sparse_points == oracle.sparse_num_points(d, n)
+    assert plan.total_points == sum(oracle.num_points(l) for l in lv)
+
+
+def _grids(lv, dtype, seed0=1000):
+    return [torch.tensor(inputs.scheme_grid(l, seed0 + g), dtype=dtype, device="cuda") for g, l in enumerate(lv)]
+
+
+@pytest.mark.parametrize("d,n", [(2, 6), (3, 5), (4, 5), (2, 12), (5, 3)])
+@pytest.mark.parametrize("op", [gbh.GBH_HIERARCHIZE, gbh.GBH_DEHIERARCHIZE])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_transform(d, n, op, dtype):
+    plan = gbh.Plan.scheme(d, n, dtype=str(dtype))
+    lv = plan.levels()
+    grids = _grids(lv, dtype)
+    host = [g.cpu().double().numpy() for g in grids]
+    plan.bind(grids)
+    plan.execute(op)
+    assert plan.status() == 0
+    fn = oracle.hierarchize if op == gbh.GBH_HIERARCHIZE else oracle.dehierarchize
+    tol = 1e-13 if dtype == torch.float64 else 1e-5
+    for l, g, u in zip(lv, grids, host):
+        assert rel_err(g.cpu().double().numpy(), fn(u, l), u) <= tol, tuple(l)
+
+
+def test_batched_round_trip_twice():
+    plan = gbh.Plan.scheme(3, 6)
+    grids = _grids(plan.levels(), torch.float64)
+    ref = [g.clone() for g in grids]
+    plan.bind(grids)
+    for _ in range(2):
+        plan.execute(gbh.GBH_HIERARCHIZE)
+        plan.execute(gbh.GBH_DEHIERARCHIZE)
+    assert plan.status() == 0
+    for g, r in zip(grids, ref):
+        assert (g - r).abs().max().item() <= 1e-13
+
+
+def test_batched_arbitrary_levels_with_zero_levels():
+    levels = np.array([[3, 0, 2], [0, 0, 0], [5, 1, 0], [2, 2, 2], [0, 4, 1]], dtype=np.int32)
+    plan = gbh.Plan.from_levels(levels)
+    grids = _grids(levels, torch.float64)
+    host = [g.cpu().numpy() for g in grids]
+    plan.bind(grids)
+    plan.execute(gbh.GBH_HIERARCHIZE)
+    assert plan.status() == 0
+    for l, g, u in zip(levels, grids, host):
+        assert rel_err(g.cpu().numpy(), oracle.hierarchize(u, l), u) <= 1e-13
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 4), (4, 4), (2, 9)])
+def test_gather_bit_exact_on_oracle_surpluses(d, n):
+    """Same surpluses in, same summation order: the fp64 gather is bit-exact."""
+    plan = gbh.Plan.scheme(d, n)
+    lv, c = oracle.scheme(d, n)
+    alphas = [oracle.hierarchize(inputs.scheme_grid(l, 1000 + g), l) for g, l in enumerate(lv)]
+    grids = [torch.tensor(a, device="cuda") for a in alphas]
+    plan.bind(grids)
+    sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
+    plan.gather(sparse)
+    ref = oracle.gather(d, n, lv, c, alphas)
+    assert np.array_equal(sparse.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_hierarchize_then_gather(dtype):
+    d, n = 3, 5
+    plan = gbh.Plan.scheme(d, n, dtype=str(dtype))
+    lv, c = oracle.scheme(d, n)
+    grids = _grids(lv, dtype)
+    host = [g.cpu().double().numpy() for g in grids]
+    plan.bind(grids)
+    plan.execute(gbh.GBH_HIERARCHIZE)
+    sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
+    plan.gather(sparse)
+    ref = oracle.gather(d, n, lv, c, [oracle.hierarchize(u, l) for u, l in zip(host, lv)])
+    tol = 1e-13 if dtype == torch.float64 else 1e-5
+    scale = max(np.abs(h).max() for h in host)
+    assert np.abs(sparse.cpu().numpy() - ref).max() <= tol * scale * 8
+
+
+def test_gather_partition_of_unity():
+    d, n = 4, 6
+    plan = gbh.Plan.scheme(d, n)
+    grids = [torch.ones(oracle.num_points(l), dtype=torch.float64, device="cuda") for l in plan.levels()]
+    plan.bind(grids)
+    sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
+    plan.gather(sparse)
+    assert torch.equal(sparse, torch.ones_like(sparse))
+
+
+def test_full_scheme_d4_n14_sampled():
+    """The full batched workload (1665 grids, 218.8 M points): sampled grids
+    against the oracle."""
+    plan = gbh.Plan.scheme(4, 14)
+    lv = plan.levels()
+    rng = np.random.default_rng(0)
+    picks = set(int(v) for v in rng.choice(len(lv), 12, replace=False)) | {0, len(lv) - 1}
+    grids = []
+    for g, l in enumerate(lv):
+        t = torch.empty(oracle.num_points(l), dtype=torch.float64, device="cuda")
+        if g in picks:
+            t.copy_(torch.from_numpy(inputs.scheme_grid(l, 1000 + g)))
+        else:
+            t.uniform_(-1, 1)
+        grids.append(t)
+    host = {g: grids[g].cpu().numpy() for g in picks}
+    plan.bind(grids)
+    plan.execute(gbh.GBH_HIERARCHIZE)
+    assert plan.status() == 0
+    for g in picks:
+        assert rel_err(grids[g].cpu().numpy(), oracle.hierarchize(host[g], lv[g]), host[g]) <= 1e-13
