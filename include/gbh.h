@@ -200,6 +200,29 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream);
  */
 int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream);
 
+/*
+ * Batched transform that allocates nothing, for callers that may not call
+ * cudaMalloc (a framework's caching allocator owns the device, a strict memory
+ * budget, or a context where allocation is not allowed).  The paper has no
+ * counterpart: it is a variant of gbh_plan_execute whose work queue, counters
+ * and per-grid tables live in one fixed device array of 4 MiB inside the
+ * library (held by every GPU that loads the library until exit) instead of in
+ * a plan.
+ *   n_grids   : 1..2048 grids; levels: host array [n_grids][d], d in [1, 8]
+ *   grid_ptrs : HOST array of n_grids DEVICE pointers (grid g holds
+ *               prod_k (2^{l_k}+1) elements of dtype), transformed in place
+ *   op        : GBH_HIERARCHIZE or GBH_DEHIERARCHIZE
+ * Results are the same as those of a plan for the same grids.  Returns
+ * GBH_ERANGE when the grids need more work items than the array holds
+ * (roughly 80,000 items of 65,536 points).  The first call on a device looks
+ * up the array's device address; make that call before any stream capture.
+ * Every call rewrites the shared array and clears its counters: calls whose
+ * kernels overlap on the GPU (other streams, other threads) race, so order
+ * them on one stream.  Not thread-safe on the host.
+ */
+int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, void *const *grid_ptrs,
+                                  int dtype, int op, void *stream);
+
 /* Sticky device-side status of a plan (GBH_ETIMEOUT after an expired wait);
  * synchronises the stream given.  Reading it clears it. */
 int gbh_plan_status(gbh_plan *plan, void *stream);

@@ -871,3 +871,196 @@ int gbh_plan_status(gbh_plan *plan, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched transform without any allocation
+// ---------------------------------------------------------------------------
+//
+// For callers that must not allocate device memory: code that runs while a
+// framework's caching allocator owns the whole device, code inside a memory
+// budget that forbids hidden allocations, or code that may not call
+// cudaMalloc at all at that point.  The work queue, its counters and the
+// per-grid tables live in one file-scope device array of fixed size instead of
+// in a plan; the kernel is the plan's k_batched.  The array's device address
+// is looked up once per device (the first call on a device does this, so that
+// call should come before any stream capture).  Every call shares the array
+// and rewrites it: calls that overlap on the GPU race; the counters are
+// cleared by every call.
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 4u << 20;        // device work tables, per device
+constexpr int kNoAllocMaxGrids = 2048;
+constexpr int64_t kNoAllocItemPoints = 65536;      // points per work item
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocHost {
+    GridInfo info[kNoAllocMaxGrids];
+    int need[kNoAllocMaxGrids * kPhases];
+    void *ptrs[kNoAllocMaxGrids];
+    int order[kNoAllocMaxGrids];
+    Item items[kNoAllocBytes / sizeof(Item)];
+};
+static NoAllocHost g_na_host;                      // host staging, no heap
+static unsigned char *g_na_dev[64];                // symbol address per device
+
+size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+
+// Items of grid g, phase ph (same decomposition as grid_items, larger items).
+bool na_items(const GridInfo &gi, int g, int d, int ph, int wait, int &nitems, int cap, int &cnt)
+{
+    cnt = 0;
+    auto push = [&](int kind, int dim, int64_t s, int64_t c) {
+        if (nitems >= cap) return false;
+        g_na_host.items[nitems++] = Item{g, ph, kind, dim, s, c, wait, 0};
+        ++cnt;
+        return true;
+    };
+    if (ph == 0) {
+        for (int64_t s = 0; s < gi.N; s += kNoAllocItemPoints)
+            if (!push(K_SCAN, 0, s, std::min<int64_t>(kNoAllocItemPoints, gi.N - s))) return false;
+        return true;
+    }
+    const int k = ph - 1;
+    if (k >= d || gi.l[k] == 0) return true;
+    const int64_t n = ((int64_t)1 << gi.l[k]) + 1, poles = gi.N / n;
+    if (k == 0 && n <= kRowsSmemElems) {
+        const int64_t rpi = std::max<int64_t>(1, kRowsSmemElems / n);
+        for (int64_t s = 0; s < poles; s += rpi)
+            if (!push(K_ROWS, 0, s, std::min(rpi, poles - s))) return false;
+        return true;
+    }
+    if (gi.l[k] > 5 && (poles < 4 * kBThreads || k == 0)) {
+        const int64_t ppi = std::max<int64_t>(1, kNoAllocItemPoints / n);
+        for (int64_t s = 0; s < poles; s += ppi)
+            if (!push(K_LONG, k, s, std::min(ppi, poles - s))) return false;
+        return true;
+    }
+    const int64_t ppi = std::max<int64_t>(kBThreads, kNoAllocItemPoints / n);
+    for (int64_t s = 0; s < poles; s += ppi)
+        if (!push(K_POLES, k, s, std::min(ppi, poles - s))) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, void *const *grid_ptrs,
+                                             int dtype, int op, void *stream)
+{
+    if (!levels || !grid_ptrs || n_grids < 1 || d < 1 || d > kPlanMaxD) return GBH_EINVAL;
+    if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return op == GBH_ADJOINT ? GBH_EUNSUPPORTED : GBH_EINVAL;
+    if (n_grids > kNoAllocMaxGrids) return GBH_ERANGE;
+    const size_t es = dtype == GBH_F64 ? 8 : 4;
+    // per-grid geometry
+    for (int g = 0; g < n_grids; ++g) {
+        if (!grid_ptrs[g]) return GBH_EINVAL;
+        if (reinterpret_cast<uintptr_t>(grid_ptrs[g]) % es) return GBH_EALIGN;
+        GridInfo &gi = g_na_host.info[g];
+        std::memset(&gi, 0, sizeof(gi));
+        gi.first_dim = gi.last_dim = -1;
+        int64_t N = 1;
+        double growth = 1.0;
+        for (int k = 0; k < d; ++k) {
+            const int l = levels[(size_t)g * d + k];
+            if (l < 0 || l > 30) return GBH_ERANGE;
+            const int64_t nk = ((int64_t)1 << l) + 1;
+            if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
+            gi.l[k] = l;
+            gi.S[k] = N;
+            N *= nk;
+            if (l > 0) {
+                if (gi.first_dim < 0) gi.first_dim = k;
+                gi.last_dim = k;
+                ++gi.passes;
+                growth *= dgrowth(std::min(l, 16));
+            }
+        }
+        gi.N = N;
+        gi.g0 = 61 - 2 * gi.passes;
+        gi.g0_d = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
+        g_na_host.ptrs[g] = grid_ptrs[g];
+        g_na_host.order[g] = g;
+    }
+    // device layout: counters | need | ptrs | info | items
+    const size_t o_ticket = 0, o_status = 32, o_emax = 64;
+    const size_t o_done = na_align(o_emax + sizeof(int) * (size_t)n_grids);
+    const size_t o_need = na_align(o_done + sizeof(int) * (size_t)n_grids * kPhases);
+    const size_t o_ptrs = na_align(o_need + sizeof(int) * (size_t)n_grids * kPhases);
+    const size_t o_info = na_align(o_ptrs + sizeof(void *) * (size_t)n_grids);
+    const size_t o_items = na_align(o_info + sizeof(GridInfo) * (size_t)n_grids);
+    if (o_items >= kNoAllocBytes) return GBH_ERANGE;
+    const int cap = (int)std::min<size_t>((kNoAllocBytes - o_items) / sizeof(Item),
+                                          sizeof(g_na_host.items) / sizeof(Item));
+    // items: waves of grids that fit in L2 together, phase-major inside a wave
+    std::sort(g_na_host.order, g_na_host.order + n_grids,
+              [](int a, int b) { return g_na_host.info[a].N > g_na_host.info[b].N || (g_na_host.info[a].N == g_na_host.info[b].N && a < b); });
+    std::memset(g_na_host.need, 0, sizeof(int) * (size_t)n_grids * kPhases);
+    int nitems = 0;
+    int w0 = 0;
+    int prev[kNoAllocMaxGrids];
+    while (w0 < n_grids) {
+        int w1 = w0;
+        double bytes = 0.0;
+        while (w1 < n_grids && (w1 == w0 || bytes + (double)g_na_host.info[g_na_host.order[w1]].N * es <= kWaveBytes)) {
+            bytes += (double)g_na_host.info[g_na_host.order[w1]].N * es;
+            ++w1;
+        }
+        for (int w = w0; w < w1; ++w) prev[w] = -1;
+        for (int ph = (dtype == GBH_F64 ? 0 : 1); ph < kPhases; ++ph)
+            for (int w = w0; w < w1; ++w) {
+                const int g = g_na_host.order[w];
+                if (g_na_host.info[g].first_dim < 0) continue;
+                int cnt = 0;
+                if (!na_items(g_na_host.info[g], g, d, ph, prev[w], nitems, cap, cnt)) return GBH_ERANGE;
+                g_na_host.need[g * kPhases + ph] = cnt;
+                if (cnt > 0) prev[w] = ph;
+            }
+        w0 = w1;
+    }
+    // set-up: the array's device address, once per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GBH_ECUDA;
+    if (!g_na_dev[dev]) {
+        unsigned char *ptr = nullptr;
+        if (cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch) != cudaSuccess || !ptr)
+            return GBH_ECUDA;
+        g_na_dev[dev] = ptr;
+    }
+    unsigned char *base = g_na_dev[dev];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // counters start at zero; the tables are rewritten by every call
+    if (cudaMemsetAsync(base, 0, o_need, s) != cudaSuccess) return GBH_ECUDA;
+    if (cudaMemcpyAsync(base + o_need, g_na_host.need, sizeof(int) * (size_t)n_grids * kPhases, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(base + o_ptrs, g_na_host.ptrs, sizeof(void *) * (size_t)n_grids, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(base + o_info, g_na_host.info, sizeof(GridInfo) * (size_t)n_grids, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(base + o_items, g_na_host.items, sizeof(Item) * (size_t)nitems, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GBH_ECUDA;
+    BatchParams P{};
+    P.items = reinterpret_cast<const Item *>(base + o_items);
+    P.nitems = nitems;
+    P.grids = reinterpret_cast<const GridInfo *>(base + o_info);
+    P.ptrs = reinterpret_cast<void *const *>(base + o_ptrs);
+    P.ticket = reinterpret_cast<unsigned *>(base + o_ticket);
+    P.status = reinterpret_cast<int *>(base + o_status);
+    P.emax = reinterpret_cast<int *>(base + o_emax);
+    P.done = reinterpret_cast<int *>(base + o_done);
+    P.need = reinterpret_cast<const int *>(base + o_need);
+    P.op = op;
+    if (nitems == 0) return GBH_OK;
+    const size_t smem = kRowsSmemElems * es;
+    auto launch = [&](auto kern) -> int {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem);
+        if (per_sm < 1) return GBH_EUNSUPPORTED;
+        const int grid = std::max(1, std::min(num_sms() * per_sm, nitems));
+        kern<<<grid, kBThreads, smem, s>>>(P);
+        count_launches(1);
+        return check_launch();
+    };
+    if (dtype == GBH_F64)
+        return op == GBH_HIERARCHIZE ? launch(k_batched<double, OP_H>) : launch(k_batched<double, OP_D>);
+    return op == GBH_HIERARCHIZE ? launch(k_batched<float, OP_H>) : launch(k_batched<float, OP_D>);
+}
