@@ -228,6 +228,115 @@ def forms(args, dev, hbm):
         measure(f"fwd_{nm}_16x_8_8_8", t, lv5, gbh.GBH_HIERARCHIZE, 5, es, batch=16)
         del t
     torch.cuda.empty_cache()
+    out.update(scheme_forms(dev, hbm))
+    out.update(autograd_forms(dev, hbm))
+    return out
+
+
+def _ms(fn, reps, restore=None):
+    import torch
+    st = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if restore is not None:
+            restore()
+    return float(np.median(times))
+
+
+def scheme_forms(dev, hbm):
+    """Batched combination scheme d=4, n=14 (1665 grids, 218.8 M points):
+    one persistent launch for all grids, the fp64 gather into the sparse grid
+    (25.4 M points), and both captured in one CUDA graph."""
+    import torch
+
+    import paper_1309_0392_gb300 as gbh
+    out = {}
+    for dt, es, nm in ((torch.float64, 8, "fp64"), (torch.float32, 4, "fp32")):
+        plan = gbh.Plan.scheme(4, 14, dtype=str(dt))
+        lv = plan.levels()
+        gen = torch.Generator(device=dev).manual_seed(1000)
+        grids = [torch.empty(gbh.num_points(l), dtype=dt, device=dev).uniform_(-1, 1, generator=gen) for l in lv]
+        plan.bind(grids)
+        sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device=dev)
+        P = plan.total_points
+        H, D = gbh.GBH_HIERARCHIZE, gbh.GBH_DEHIERARCHIZE
+        for _ in range(3):
+            plan.execute(H)
+            plan.execute(D)
+        torch.cuda.synchronize()
+        ms = _ms(lambda: plan.execute(H), 5, restore=lambda: plan.execute(D))
+        out[f"batched_{nm}_d4_n14"] = {"Gpts_s": P / (ms * 1e-3) / 1e9, "GB_s": 2 * es * P / (ms * 1e-3) / 1e9,
+                                       "frac_of_hbm": 2 * es * P / (ms * 1e-3) / 1e9 / hbm, "ms": ms,
+                                       "points": P, "grids": len(lv)}
+        ms_d = _ms(lambda: plan.execute(D), 5, restore=lambda: plan.execute(H))
+        out[f"batched_dehier_{nm}_d4_n14"] = {"Gpts_s": P / (ms_d * 1e-3) / 1e9,
+                                              "frac_of_hbm": 2 * es * P / (ms_d * 1e-3) / 1e9 / hbm, "ms": ms_d}
+        plan.execute(H)
+        ms_g = _ms(lambda: plan.gather(sparse), 5)
+        gb = (es * P + 8 * plan.sparse_points) / (ms_g * 1e-3) / 1e9
+        out[f"gather_{nm}_d4_n14"] = {"ms": ms_g, "GB_s": gb, "frac_of_hbm": gb / hbm,
+                                      "sparse_points": plan.sparse_points}
+        plan.execute(D)
+        # one CUDA graph: hierarchize every grid, then gather
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.execute(H)
+            plan.execute(D)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            plan.execute(H)
+            plan.gather(sparse)
+        ms_graph = _ms(lambda: g.replay(), 5, restore=lambda: plan.execute(D))
+        out[f"batched_gather_graph_{nm}_d4_n14"] = {"ms": ms_graph, "Gpts_s": P / (ms_graph * 1e-3) / 1e9,
+                                                    "status": plan.status()}
+        del g, grids, sparse, plan
+        torch.cuda.empty_cache()
+    return out
+
+
+def autograd_forms(dev, hbm):
+    """Differentiation workload: 16 grids of level (8,8,8); one forward and
+    backward through HierarchizeFn of the weighted surplus loss."""
+    import torch
+
+    from paper_1309_0392_gb300 import inputs
+    from paper_1309_0392_gb300.autograd import HierarchizeFn
+    out = {}
+    levels, u = inputs.cfg5()
+    B, n = u.shape
+    w1 = []
+    for l in levels:
+        i = np.arange(2 ** l + 1)
+        lev = np.zeros_like(i)
+        inner = (i > 0) & (i < 2 ** l)
+        lev[inner] = l - np.array([(int(v) & -int(v)).bit_length() - 1 for v in i[inner]])
+        w1.append(2.0 ** -lev)
+    w = torch.ones(1, dtype=torch.float64, device=dev)
+    for v in reversed(w1):
+        w = torch.kron(w, torch.tensor(v, device=dev))
+    for dt, nm in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+        x = torch.tensor(u, dtype=dt, device=dev, requires_grad=True)
+        wd = w.to(dt)
+
+        def step():
+            x.grad = None
+            a = HierarchizeFn.apply(x, levels)
+            (wd * a * a).sum().backward()
+
+        step()
+        ms = _ms(step, 5)
+        out[f"autograd_step_{nm}_16x_8_8_8"] = {"ms": ms, "Gpts_s": B * n / (ms * 1e-3) / 1e9}
+        del x
+    torch.cuda.empty_cache()
     return out
 
 
