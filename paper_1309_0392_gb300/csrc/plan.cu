@@ -143,8 +143,81 @@ __device__ __forceinline__ F fl_op(F v, F L, F R)
     return v + F(0.5) * (L + R);
 }
 
+// A pole of level L held in registers: hierarchize (fine to coarse) or
+// dehierarchize (coarse to fine); fixed point (long long) or fp32.
+template <typename V, int L, int OP>
+__device__ __forceinline__ void b_pole_regs(V *v)
+{
+    constexpr int last = 1 << L;
+    constexpr bool FX = std::is_same<V, long long>::value;
+    if constexpr (OP == OP_H) {
+#pragma unroll
+        for (int lev = L; lev >= 1; --lev) {
+            const int s = 1 << (L - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) {
+                if constexpr (FX) v[i] = fx_op<OP>(v[i], v[i - s], v[i + s]);
+                else v[i] = fl_op<OP>(v[i], v[i - s], v[i + s]);
+            }
+        }
+        if constexpr (FX) {
+            v[0] = v[0] + v[0];
+            v[last] = v[last] + v[last];
+        }
+    } else {
+#pragma unroll
+        for (int lev = 1; lev <= L; ++lev) {
+            const int s = 1 << (L - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) {
+                if constexpr (FX) v[i] = fx_op<OP>(v[i], v[i - s], v[i + s]);
+                else v[i] = fl_op<OP>(v[i], v[i - s], v[i + s]);
+            }
+        }
+    }
+}
+
+// rows of level L staged in shared memory, one thread per row
+template <typename V, int L, int OP>
+__device__ __forceinline__ void b_rows_regs(V *sv, int rows)
+{
+    constexpr int n = (1 << L) + 1;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        V v[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = sv[r * n + i];
+        b_pole_regs<V, L, OP>(v);
+#pragma unroll
+        for (int i = 0; i < n; ++i) sv[r * n + i] = v[i];
+    }
+}
+
+// poles of level L along a dimension of stride S, one thread per pole, loads
+// and stores all independent (the data of one phase stays in L2)
+template <typename ST, typename V, int L, int OP, typename AccT>
+__device__ __forceinline__ void b_poles_regs(const AccT &A, ST *base, int64_t S, int64_t start, int64_t count)
+{
+    constexpr int n = (1 << L) + 1;
+    for (int64_t t = start + threadIdx.x; t < start + count; t += blockDim.x) {
+        const int64_t o = t / S, j = t - o * S;
+        const int64_t pb = o * S * n + j;
+        V v[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            if constexpr (sizeof(ST) == 8) v[i] = A.rd(pb + i * S);
+            else v[i] = __ldcg(base + pb + i * S);
+        }
+        b_pole_regs<V, L, OP>(v);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            if constexpr (sizeof(ST) == 8) A.wr(pb + i * S, v[i]);
+            else __stcg(base + pb + i * S, v[i]);
+        }
+    }
+}
+
 template <typename ST, int OP>
-__global__ void __launch_bounds__(kBThreads) k_batched(const BatchParams P)
+__global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_item;
@@ -209,7 +282,16 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const BatchParams P)
                 }
                 __syncthreads();
                 const int rows = (int)it.count;
-                if (OP == OP_H) {
+                if (l <= 5) {
+                    switch (l) {
+                        case 1: b_rows_regs<V, 1, OP>(sv, rows); break;
+                        case 2: b_rows_regs<V, 2, OP>(sv, rows); break;
+                        case 3: b_rows_regs<V, 3, OP>(sv, rows); break;
+                        case 4: b_rows_regs<V, 4, OP>(sv, rows); break;
+                        default: b_rows_regs<V, 5, OP>(sv, rows); break;
+                    }
+                    __syncthreads();
+                } else if (OP == OP_H) {
                     for (int lev = l; lev >= 1; --lev) {
                         const int s = 1 << (l - lev), per = 1 << (lev - 1);
                         for (int q = tid; q < rows * per; q += blockDim.x) {
@@ -242,6 +324,14 @@ __global__ void __launch_bounds__(kBThreads) k_batched(const BatchParams P)
                 for (int e = tid; e < cnt; e += blockDim.x) {
                     if constexpr (sizeof(ST) == 8) A.wr(e0 + e, sv[e]);
                     else __stcg(base + e0 + e, sv[e]);
+                }
+            } else if (it.kind == K_POLES && l <= 5) {
+                switch (l) {
+                    case 1: b_poles_regs<ST, V, 1, OP>(A, base, S, it.start, it.count); break;
+                    case 2: b_poles_regs<ST, V, 2, OP>(A, base, S, it.start, it.count); break;
+                    case 3: b_poles_regs<ST, V, 3, OP>(A, base, S, it.start, it.count); break;
+                    case 4: b_poles_regs<ST, V, 4, OP>(A, base, S, it.start, it.count); break;
+                    default: b_poles_regs<ST, V, 5, OP>(A, base, S, it.start, it.count); break;
                 }
             } else if (it.kind == K_POLES) {
                 // one thread per pole, level by level in place (L2-resident)

@@ -20,17 +20,10 @@ def level_weights_torch(levels, device):
     """w = prod_k 2^{-level_k(i_k)} as a flat tensor (dimension 0 fastest)."""
     w = torch.ones(1, dtype=torch.float64, device=device)
     for l in reversed(levels):
-        i = torch.arange(2 ** l + 1, device=device)
-        lev = torch.zeros_like(i)
-        inner = (i > 0) & (i < 2 ** l)
-        tz = torch.zeros_like(i)
-        v = i.clone()
-        for _ in range(l):
-            even = inner & (v % 2 == 0)
-            tz = tz + even.long()
-            v = torch.where(even, v // 2, v)
-        lev[inner] = l - tz[inner]
-        w = torch.kron(w, torch.pow(2.0, -lev.double()))
+        lev = np.zeros(2 ** l + 1)
+        for i in range(1, 2 ** l):
+            lev[i] = l - ((i & -i).bit_length() - 1)
+        w = torch.kron(w, torch.tensor(2.0 ** -lev, device=device))
     return w
 
 
