@@ -158,9 +158,9 @@ typedef struct gbh_plan gbh_plan;
 int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out);
 
 /*
- * Plan for an arbitrary list of grids: levels is a host array [n_grids][d].
- * Coefficients are 1 unless set with gbh_plan_set_coeffs; gbh_plan_gather
- * needs a plan made by gbh_plan_create_scheme.
+ * Plan for an arbitrary list of grids: levels is a host array [n_grids][d],
+ * d in [1, 8], every level in [0, 17] (GBH_ERANGE otherwise).  Coefficients
+ * are 1; gbh_plan_gather needs a plan made by gbh_plan_create_scheme.
  */
 int gbh_plan_create(int n_grids, int d, const int32_t *levels, int dtype, gbh_plan **out);
 

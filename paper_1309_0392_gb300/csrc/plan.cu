@@ -29,13 +29,12 @@ namespace {
 
 constexpr int kPlanMaxD = 8;
 constexpr int kBThreads = 256;
-constexpr int kRowsSmemElems = 8192;          // staged elements per rows item
-constexpr int64_t kItemPoints = 16384;        // target points per item
+constexpr int64_t kItemPoints = 32768;        // target points per item
 constexpr double kWaveBytes = 48.0 * 1024 * 1024;
 constexpr long long kSpinLimit = 1ll << 24;   // bounded waits (~ seconds)
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
-enum ItemKind { K_SCAN = 0, K_ROWS = 1, K_POLES = 2, K_LONG = 3 };
+enum ItemKind { K_SCAN = 0, K_CONV_IN = 1, K_CONV_OUT = 2, K_ROWS = 3, K_POLES = 4, K_GROUP = 5, K_LATT = 6 };
 
 struct GridInfo {
     int l[kPlanMaxD];
@@ -56,7 +55,7 @@ struct Item {
     int64_t start;       // first row / pole / element
     int64_t count;
     int wait;            // phase that must be complete first (-1: none)
-    int pad;
+    int blk;             // block index (K_GROUP)
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -103,32 +102,15 @@ struct BatchParams {
     int *status;
     int op;
 };
-constexpr int kPhases = 1 + kPlanMaxD;
 
-// value access for the three storage states of an fp64 grid: the first sweep
-// reads fp64 and converts, the last converts back, the others read int64.
-template <typename ST, int OP>
-struct Acc {
-    ST *p;
-    int emax, c, X;
-    bool first, last;
-    __device__ __forceinline__ long long rd(int64_t i) const
-    {
-        if constexpr (sizeof(ST) == 8) {
-            const long long raw = __ldcg(reinterpret_cast<const long long *>(p) + i);
-            return first ? b_to_fixed(__longlong_as_double(raw), emax, c) : raw;
-        } else {
-            return 0;
-        }
-    }
-    __device__ __forceinline__ void wr(int64_t i, long long v) const
-    {
-        if constexpr (sizeof(ST) == 8) {
-            long long o = last ? __double_as_longlong(b_from_fixed(v, X)) : v;
-            __stcg(reinterpret_cast<long long *>(p) + i, o);
-        }
-    }
-};
+// Phases of a grid: 0 exponent scan and 1 conversion to fixed point (fp64
+// only), then two sub-phases per dimension (a long dimension splits into a
+// block part and a coarse-lattice part), then the conversion back.
+constexpr int kPhases = 3 + 2 * kPlanMaxD;
+constexpr int kPhaseOut = kPhases - 1;
+__host__ __device__ constexpr int dim_phase(int k, int sub) { return 2 + 2 * k + sub; }
+constexpr int kGroupLevel = 12;                  // block level of long dimensions
+constexpr int kGroupElems = 8208;               // shared-memory elements per item
 
 template <int OP>
 __device__ __forceinline__ long long fx_op(long long v, long long L, long long R)
@@ -142,25 +124,28 @@ __device__ __forceinline__ F fl_op(F v, F L, F R)
     if (OP == OP_H) return v - F(0.5) * (L + R);
     return v + F(0.5) * (L + R);
 }
+template <int OP, typename V>
+__device__ __forceinline__ V any_op(V v, V L, V R)
+{
+    if constexpr (std::is_same<V, long long>::value) return fx_op<OP>(v, L, R);
+    else return fl_op<OP, V>(v, L, R);
+}
 
 // A pole of level L held in registers: hierarchize (fine to coarse) or
-// dehierarchize (coarse to fine); fixed point (long long) or fp32.
+// dehierarchize (coarse to fine).  Fixed point doubles the two ends too, so
+// one sweep scales every point by 2.
 template <typename V, int L, int OP>
 __device__ __forceinline__ void b_pole_regs(V *v)
 {
     constexpr int last = 1 << L;
-    constexpr bool FX = std::is_same<V, long long>::value;
     if constexpr (OP == OP_H) {
 #pragma unroll
         for (int lev = L; lev >= 1; --lev) {
             const int s = 1 << (L - lev);
 #pragma unroll
-            for (int i = s; i < last; i += 2 * s) {
-                if constexpr (FX) v[i] = fx_op<OP>(v[i], v[i - s], v[i + s]);
-                else v[i] = fl_op<OP>(v[i], v[i - s], v[i + s]);
-            }
+            for (int i = s; i < last; i += 2 * s) v[i] = any_op<OP>(v[i], v[i - s], v[i + s]);
         }
-        if constexpr (FX) {
+        if constexpr (std::is_same<V, long long>::value) {
             v[0] = v[0] + v[0];
             v[last] = v[last] + v[last];
         }
@@ -169,15 +154,11 @@ __device__ __forceinline__ void b_pole_regs(V *v)
         for (int lev = 1; lev <= L; ++lev) {
             const int s = 1 << (L - lev);
 #pragma unroll
-            for (int i = s; i < last; i += 2 * s) {
-                if constexpr (FX) v[i] = fx_op<OP>(v[i], v[i - s], v[i + s]);
-                else v[i] = fl_op<OP>(v[i], v[i - s], v[i + s]);
-            }
+            for (int i = s; i < last; i += 2 * s) v[i] = any_op<OP>(v[i], v[i - s], v[i + s]);
         }
     }
 }
 
-// rows of level L staged in shared memory, one thread per row
 template <typename V, int L, int OP>
 __device__ __forceinline__ void b_rows_regs(V *sv, int rows)
 {
@@ -192,26 +173,75 @@ __device__ __forceinline__ void b_rows_regs(V *sv, int rows)
     }
 }
 
-// poles of level L along a dimension of stride S, one thread per pole, loads
-// and stores all independent (the data of one phase stays in L2)
-template <typename ST, typename V, int L, int OP, typename AccT>
-__device__ __forceinline__ void b_poles_regs(const AccT &A, ST *base, int64_t S, int64_t start, int64_t count)
+// `count` poles starting at pole `start`: pole t of a dimension with stride S
+// and extent n starts at (t / S) S n + t % S; the pole's points sit at stride
+// `st` from there (a coarse lattice uses st = 2^m S).  One thread per pole,
+// loads and stores all independent.
+template <typename V, int L, int OP>
+__device__ __forceinline__ void b_poles_regs(V *base, int64_t S, int64_t n, int64_t st, int64_t start, int64_t count)
 {
-    constexpr int n = (1 << L) + 1;
+    constexpr int np = (1 << L) + 1;
     for (int64_t t = start + threadIdx.x; t < start + count; t += blockDim.x) {
         const int64_t o = t / S, j = t - o * S;
-        const int64_t pb = o * S * n + j;
-        V v[n];
+        V *pp = base + o * S * n + j;
+        V v[np];
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
-            if constexpr (sizeof(ST) == 8) v[i] = A.rd(pb + i * S);
-            else v[i] = __ldcg(base + pb + i * S);
-        }
+        for (int i = 0; i < np; ++i) v[i] = __ldcg(pp + i * st);
         b_pole_regs<V, L, OP>(v);
 #pragma unroll
-        for (int i = 0; i < n; ++i) {
-            if constexpr (sizeof(ST) == 8) A.wr(pb + i * S, v[i]);
-            else __stcg(base + pb + i * S, v[i]);
+        for (int i = 0; i < np; ++i) __stcg(pp + i * st, v[i]);
+    }
+}
+
+template <typename V, int OP>
+__device__ __forceinline__ void b_poles_dispatch(int L, V *base, int64_t S, int64_t n, int64_t st, int64_t start,
+                                                 int64_t count)
+{
+    switch (L) {
+        case 1: b_poles_regs<V, 1, OP>(base, S, n, st, start, count); break;
+        case 2: b_poles_regs<V, 2, OP>(base, S, n, st, start, count); break;
+        case 3: b_poles_regs<V, 3, OP>(base, S, n, st, start, count); break;
+        case 4: b_poles_regs<V, 4, OP>(base, S, n, st, start, count); break;
+        case 5: b_poles_regs<V, 5, OP>(base, S, n, st, start, count); break;
+        default: break;
+    }
+}
+
+// Level-ordered sweep of `rows` poles of level L staged in shared memory
+// (pole r at sv + r * pitch); with `ends` the two ends are doubled (fixed
+// point) at the end.
+template <typename V, int OP>
+__device__ __forceinline__ void b_smem_sweep(V *sv, int rows, int pitch, int L, bool ends)
+{
+    const int last = 1 << L;
+    if (OP == OP_H) {
+        for (int lev = L; lev >= 1; --lev) {
+            const int s = 1 << (L - lev), per = 1 << (lev - 1);
+            for (int q = threadIdx.x; q < rows * per; q += blockDim.x) {
+                const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                V *row = sv + r * pitch;
+                row[i] = any_op<OP>(row[i], row[i - s], row[i + s]);
+            }
+            __syncthreads();
+        }
+        if constexpr (std::is_same<V, long long>::value) {
+            if (ends) {
+                for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+                    sv[r * pitch] += sv[r * pitch];
+                    sv[r * pitch + last] += sv[r * pitch + last];
+                }
+                __syncthreads();
+            }
+        }
+    } else {
+        for (int lev = 1; lev <= L; ++lev) {
+            const int s = 1 << (L - lev), per = 1 << (lev - 1);
+            for (int q = threadIdx.x; q < rows * per; q += blockDim.x) {
+                const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                V *row = sv + r * pitch;
+                row[i] = any_op<OP>(row[i], row[i - s], row[i + s]);
+            }
+            __syncthreads();
         }
     }
 }
@@ -248,184 +278,75 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
         if (idx >= P.nitems || s_abort || ld_acquire(P.status) != 0) return;
         const Item it = P.items[idx];
         const GridInfo &gi = P.grids[it.grid];
-        ST *base = reinterpret_cast<ST *>(P.ptrs[it.grid]);
+        ST *sbase = reinterpret_cast<ST *>(P.ptrs[it.grid]);
+        V *base = reinterpret_cast<V *>(P.ptrs[it.grid]);
 
         if (it.kind == K_SCAN) {
             int em = 0;
-            const long long *b = reinterpret_cast<const long long *>(base);
+            const long long *b = reinterpret_cast<const long long *>(sbase);
             for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
                 const int e = (int)((__ldcg(b + i) >> 52) & 0x7FF);
                 em = e > em ? e : em;
             }
             em = __reduce_max_sync(0xFFFFFFFFu, (unsigned)em);
             if ((tid & 31) == 0 && em > 0) atomicMax(P.emax + it.grid, em);
+        } else if (it.kind == K_CONV_IN || it.kind == K_CONV_OUT) {
+            if constexpr (sizeof(ST) == 8) {
+                const int emax = ld_acquire(P.emax + it.grid);
+                const int c = (OP == OP_H ? gi.g0 : gi.g0_d) - 53;
+                const int X = emax - 1075 - c - (OP == OP_H ? gi.passes : 0);
+                long long *b = reinterpret_cast<long long *>(sbase);
+                for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
+                    const long long v = __ldcg(b + i);
+                    __stcg(b + i, it.kind == K_CONV_IN ? b_to_fixed(__longlong_as_double(v), emax, c)
+                                                       : __double_as_longlong(b_from_fixed(v, X)));
+                }
+            }
         } else {
             const int k = it.dim, l = gi.l[k];
-            const int64_t n = ((int64_t)1 << l) + 1, S = gi.S[k], last_i = (int64_t)1 << l;
-            Acc<ST, OP> A;
-            A.p = base;
-            A.first = (k == gi.first_dim);
-            A.last = (k == gi.last_dim);
-            if constexpr (sizeof(ST) == 8) {
-                A.emax = ld_acquire(P.emax + it.grid);
-                const int g0 = OP == OP_H ? gi.g0 : gi.g0_d;
-                A.c = g0 - 53;
-                A.X = A.emax - 1075 - A.c - (OP == OP_H ? gi.passes : 0);
-            }
+            const int64_t n = ((int64_t)1 << l) + 1, S = gi.S[k];
             if (it.kind == K_ROWS) {
                 // dimension 0: `count` whole rows staged in shared memory
                 const int64_t e0 = it.start * n;
                 const int cnt = (int)(it.count * n);
-                for (int e = tid; e < cnt; e += blockDim.x) {
-                    if constexpr (sizeof(ST) == 8) sv[e] = A.rd(e0 + e);
-                    else sv[e] = __ldcg(base + e0 + e);
-                }
+                for (int e = tid; e < cnt; e += blockDim.x) sv[e] = __ldcg(base + e0 + e);
                 __syncthreads();
                 const int rows = (int)it.count;
-                if (l <= 5) {
-                    switch (l) {
-                        case 1: b_rows_regs<V, 1, OP>(sv, rows); break;
-                        case 2: b_rows_regs<V, 2, OP>(sv, rows); break;
-                        case 3: b_rows_regs<V, 3, OP>(sv, rows); break;
-                        case 4: b_rows_regs<V, 4, OP>(sv, rows); break;
-                        default: b_rows_regs<V, 5, OP>(sv, rows); break;
-                    }
-                    __syncthreads();
-                } else if (OP == OP_H) {
-                    for (int lev = l; lev >= 1; --lev) {
-                        const int s = 1 << (l - lev), per = 1 << (lev - 1);
-                        for (int q = tid; q < rows * per; q += blockDim.x) {
-                            const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
-                            V *row = sv + r * n;
-                            if constexpr (sizeof(ST) == 8) row[i] = fx_op<OP>(row[i], row[i - s], row[i + s]);
-                            else row[i] = fl_op<OP>(row[i], row[i - s], row[i + s]);
-                        }
-                        __syncthreads();
-                    }
-                    if constexpr (sizeof(ST) == 8) {
-                        for (int r = tid; r < rows; r += blockDim.x) {
-                            sv[r * n] += sv[r * n];
-                            sv[r * n + last_i] += sv[r * n + last_i];
-                        }
-                        __syncthreads();
-                    }
-                } else {
-                    for (int lev = 1; lev <= l; ++lev) {
-                        const int s = 1 << (l - lev), per = 1 << (lev - 1);
-                        for (int q = tid; q < rows * per; q += blockDim.x) {
-                            const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
-                            V *row = sv + r * n;
-                            if constexpr (sizeof(ST) == 8) row[i] = fx_op<OP>(row[i], row[i - s], row[i + s]);
-                            else row[i] = fl_op<OP>(row[i], row[i - s], row[i + s]);
-                        }
-                        __syncthreads();
-                    }
-                }
-                for (int e = tid; e < cnt; e += blockDim.x) {
-                    if constexpr (sizeof(ST) == 8) A.wr(e0 + e, sv[e]);
-                    else __stcg(base + e0 + e, sv[e]);
-                }
-            } else if (it.kind == K_POLES && l <= 5) {
                 switch (l) {
-                    case 1: b_poles_regs<ST, V, 1, OP>(A, base, S, it.start, it.count); break;
-                    case 2: b_poles_regs<ST, V, 2, OP>(A, base, S, it.start, it.count); break;
-                    case 3: b_poles_regs<ST, V, 3, OP>(A, base, S, it.start, it.count); break;
-                    case 4: b_poles_regs<ST, V, 4, OP>(A, base, S, it.start, it.count); break;
-                    default: b_poles_regs<ST, V, 5, OP>(A, base, S, it.start, it.count); break;
+                    case 1: b_rows_regs<V, 1, OP>(sv, rows); __syncthreads(); break;
+                    case 2: b_rows_regs<V, 2, OP>(sv, rows); __syncthreads(); break;
+                    case 3: b_rows_regs<V, 3, OP>(sv, rows); __syncthreads(); break;
+                    case 4: b_rows_regs<V, 4, OP>(sv, rows); __syncthreads(); break;
+                    case 5: b_rows_regs<V, 5, OP>(sv, rows); __syncthreads(); break;
+                    default: b_smem_sweep<V, OP>(sv, rows, (int)n, l, true); break;
                 }
+                for (int e = tid; e < cnt; e += blockDim.x) __stcg(base + e0 + e, sv[e]);
             } else if (it.kind == K_POLES) {
-                // one thread per pole, level by level in place (L2-resident)
-                for (int64_t t = it.start + tid; t < it.start + it.count; t += blockDim.x) {
-                    const int64_t o = t / S, j = t - o * S;
-                    const int64_t pb = o * S * n + j;
-                    if constexpr (sizeof(ST) == 8) {
-                        if (A.first)
-                            for (int64_t i = 0; i <= last_i; ++i) __stcg(reinterpret_cast<long long *>(base) + pb + i * S, A.rd(pb + i * S));
-                        Acc<ST, OP> B = A;
-                        B.first = false;
-                        B.last = false;
-                        if (OP == OP_H) {
-                            for (int lev = l; lev >= 1; --lev) {
-                                const int64_t s = (int64_t)1 << (l - lev);
-                                for (int64_t i = s; i < last_i; i += 2 * s)
-                                    B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
-                            }
-                            B.wr(pb, B.rd(pb) * 2);
-                            B.wr(pb + last_i * S, B.rd(pb + last_i * S) * 2);
-                        } else {
-                            for (int lev = 1; lev <= l; ++lev) {
-                                const int64_t s = (int64_t)1 << (l - lev);
-                                for (int64_t i = s; i < last_i; i += 2 * s)
-                                    B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
-                            }
-                        }
-                        if (A.last)
-                            for (int64_t i = 0; i <= last_i; ++i) A.wr(pb + i * S, B.rd(pb + i * S));
-                    } else {
-                        ST *pp = base + pb;
-                        if (OP == OP_H) {
-                            for (int lev = l; lev >= 1; --lev) {
-                                const int64_t s = (int64_t)1 << (l - lev);
-                                for (int64_t i = s; i < last_i; i += 2 * s)
-                                    __stcg(pp + i * S, fl_op<OP>(__ldcg(pp + i * S), __ldcg(pp + (i - s) * S), __ldcg(pp + (i + s) * S)));
-                            }
-                        } else {
-                            for (int lev = 1; lev <= l; ++lev) {
-                                const int64_t s = (int64_t)1 << (l - lev);
-                                for (int64_t i = s; i < last_i; i += 2 * s)
-                                    __stcg(pp + i * S, fl_op<OP>(__ldcg(pp + i * S), __ldcg(pp + (i - s) * S), __ldcg(pp + (i + s) * S)));
-                            }
-                        }
-                    }
-                }
+                b_poles_dispatch<V, OP>(l, base, S, n, S, it.start, it.count);
+            } else if (it.kind == K_LATT) {
+                // coarse lattice of a long dimension: points a 2^m, stride 2^m S
+                const int m = l < kGroupLevel ? l : kGroupLevel;
+                b_poles_dispatch<V, OP>(l - m, base, S, n, S << m, it.start, it.count);
             } else {
-                // K_LONG: `count` long poles; the CTA sweeps them level by level
-                const int64_t npole = it.count;
-                auto pbase = [&](int64_t t) { const int64_t tt = it.start + t, o = tt / S; return o * S * n + (tt - o * S); };
-                if constexpr (sizeof(ST) == 8) {
-                    if (A.first) {
-                        for (int64_t w = tid; w < npole * n; w += blockDim.x) {
-                            const int64_t t = w % npole, i = w / npole;
-                            const int64_t a = pbase(t) + i * S;
-                            __stcg(reinterpret_cast<long long *>(base) + a, A.rd(a));
-                        }
-                        __syncthreads();
-                    }
+                // K_GROUP: block `blk` (2^m + 1 points) of `count` poles in
+                // shared memory; a block covering the whole pole writes it
+                // all, otherwise only the block interior
+                const int m = l < kGroupLevel ? l : kGroupLevel;
+                const int nb = (1 << m) + 1;
+                const int G = (int)it.count;
+                const int64_t off0 = (int64_t)it.blk << m;
+                for (int w = tid; w < G * nb; w += blockDim.x) {
+                    const int g = w % G, i = w / G;
+                    const int64_t t = it.start + g, o = t / S;
+                    sv[g * nb + i] = __ldcg(base + o * S * n + (t - o * S) + (off0 + i) * S);
                 }
-                Acc<ST, OP> B = A;
-                B.first = false;
-                B.last = false;
-                auto step = [&](int lev) {
-                    const int64_t s = (int64_t)1 << (l - lev), per = (int64_t)1 << (lev - 1);
-                    for (int64_t w = tid; w < npole * per; w += blockDim.x) {
-                        const int64_t t = w % npole, q = w / npole;
-                        const int64_t i = (2 * q + 1) * s, pb = pbase(t);
-                        if constexpr (sizeof(ST) == 8)
-                            B.wr(pb + i * S, fx_op<OP>(B.rd(pb + i * S), B.rd(pb + (i - s) * S), B.rd(pb + (i + s) * S)));
-                        else
-                            __stcg(base + pb + i * S, fl_op<OP>(__ldcg(base + pb + i * S), __ldcg(base + pb + (i - s) * S),
-                                                                __ldcg(base + pb + (i + s) * S)));
-                    }
-                    __syncthreads();
-                };
-                if (OP == OP_H) for (int lev = l; lev >= 1; --lev) step(lev);
-                else for (int lev = 1; lev <= l; ++lev) step(lev);
-                if constexpr (sizeof(ST) == 8) {
-                    if (OP == OP_H) {
-                        for (int64_t t = tid; t < npole; t += blockDim.x) {
-                            const int64_t pb = pbase(t);
-                            B.wr(pb, B.rd(pb) * 2);
-                            B.wr(pb + last_i * S, B.rd(pb + last_i * S) * 2);
-                        }
-                        __syncthreads();
-                    }
-                    if (A.last) {
-                        for (int64_t w = tid; w < npole * n; w += blockDim.x) {
-                            const int64_t t = w % npole, i = w / npole;
-                            const int64_t a = pbase(t) + i * S;
-                            A.wr(a, B.rd(a));
-                        }
-                    }
+                __syncthreads();
+                b_smem_sweep<V, OP>(sv, G, nb, m, m == l);
+                const int lo = m == l ? 0 : 1, hi = m == l ? nb : nb - 1;
+                for (int w = tid; w < G * (hi - lo); w += blockDim.x) {
+                    const int g = w % G, i = lo + w / G;
+                    const int64_t t = it.start + g, o = t / S;
+                    __stcg(base + o * S * n + (t - o * S) + (off0 + i) * S, sv[g * nb + i]);
                 }
             }
         }
@@ -435,6 +356,55 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
             atomicAdd(P.done + it.grid * kPhases + it.phase, 1);
         }
     }
+}
+
+// Work items of one grid and phase, in the order they are handed out.  `push`
+// takes (kind, dim, start, count, blk) and returns false when full.
+template <typename Push>
+bool emit_items(const GridInfo &gi, int d, int dtype, int op, int phase, int64_t chunk, Push push)
+{
+    if (phase == 0 || phase == 1 || phase == kPhaseOut) {
+        if (dtype != GBH_F64) return true;
+        const int kind = phase == 0 ? K_SCAN : phase == 1 ? K_CONV_IN : K_CONV_OUT;
+        for (int64_t s = 0; s < gi.N; s += chunk * 2)
+            if (!push(kind, 0, s, std::min<int64_t>(chunk * 2, gi.N - s), 0)) return false;
+        return true;
+    }
+    const int k = (phase - 2) / 2, sub = (phase - 2) % 2;
+    if (k >= d || gi.l[k] == 0) return true;
+    const int l = gi.l[k];
+    const int64_t n = ((int64_t)1 << l) + 1, poles = gi.N / n;
+    if (k == 0 && n <= kGroupElems) {
+        if (sub) return true;
+        const int64_t rpi = std::max<int64_t>(1, std::min<int64_t>(kGroupElems / n, std::max<int64_t>(1, chunk / n)));
+        for (int64_t s = 0; s < poles; s += rpi)
+            if (!push(K_ROWS, 0, s, std::min(rpi, poles - s), 0)) return false;
+        return true;
+    }
+    if (l <= 5) {
+        if (sub) return true;
+        const int64_t ppi = std::max<int64_t>(kBThreads, chunk / n);
+        for (int64_t s = 0; s < poles; s += ppi)
+            if (!push(K_POLES, k, s, std::min(ppi, poles - s), 0)) return false;
+        return true;
+    }
+    const int m = std::min(l, kGroupLevel);
+    const bool split = m < l;
+    // hierarchize: blocks, then the lattice; the inverse: lattice first
+    const bool blocks_now = !split ? (sub == 0) : ((op == GBH_HIERARCHIZE) == (sub == 0));
+    if (!blocks_now) {
+        if (!split) return true;
+        const int64_t ppi = std::max<int64_t>(kBThreads, chunk >> (l - m));
+        for (int64_t s = 0; s < poles; s += ppi)
+            if (!push(K_LATT, k, s, std::min(ppi, poles - s), 0)) return false;
+        return true;
+    }
+    const int64_t nb = ((int64_t)1 << m) + 1;
+    const int64_t G = std::max<int64_t>(1, kGroupElems / nb);
+    for (int64_t a = 0; a < ((int64_t)1 << (l - m)); ++a)
+        for (int64_t s = 0; s < poles; s += G)
+            if (!push(K_GROUP, k, s, std::min(G, poles - s), (int)a)) return false;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -522,13 +492,13 @@ struct gbh_plan {
     std::vector<int32_t> levels;       // [G][d]
     std::vector<double> coeffs;
     std::vector<GridInfo> info;
-    std::vector<Item> items;
-    std::vector<int> need;             // [G][kPhases]
+    std::vector<Item> items[2];        // per op (hierarchize, dehierarchize)
+    std::vector<int> need[2];          // [G][kPhases]
     int64_t total_points = 0, sparse_points = 0;
     // device
     GridInfo *d_info = nullptr;
-    Item *d_items = nullptr;
-    int *d_need = nullptr;
+    Item *d_items[2] = {nullptr, nullptr};
+    int *d_need[2] = {nullptr, nullptr};
     void **d_ptrs = nullptr;
     double *d_coeffs = nullptr;
     unsigned char *d_scratch = nullptr;   // ticket | status | emax[G] | done[G][kPhases]
@@ -547,8 +517,10 @@ void free_plan(gbh_plan *p)
 {
     if (!p) return;
     cudaFree(p->d_info);
-    cudaFree(p->d_items);
-    cudaFree(p->d_need);
+    for (int o = 0; o < 2; ++o) {
+        cudaFree(p->d_items[o]);
+        cudaFree(p->d_need[o]);
+    }
     cudaFree(p->d_ptrs);
     cudaFree(p->d_coeffs);
     cudaFree(p->d_scratch);
@@ -570,51 +542,11 @@ int upload(T **dst, const std::vector<T> &src)
     return GBH_OK;
 }
 
-// Work items of one grid for phase p, appended to `out`.
-void grid_items(const GridInfo &gi, int g, int d, int es, int phase, std::vector<Item> &out, int &count)
-{
-    count = 0;
-    if (phase == 0) {
-        for (int64_t s = 0; s < gi.N; s += kItemPoints * 4) {
-            out.push_back(Item{g, 0, K_SCAN, 0, s, std::min<int64_t>(kItemPoints * 4, gi.N - s), -1, 0});
-            ++count;
-        }
-        return;
-    }
-    const int k = phase - 1;
-    if (k >= d || gi.l[k] == 0) return;
-    const int64_t n = ((int64_t)1 << gi.l[k]) + 1;
-    const int64_t poles = gi.N / n;
-    if (k == 0 && n <= kRowsSmemElems) {
-        const int64_t rpi = std::max<int64_t>(1, std::min<int64_t>(kRowsSmemElems / n, std::max<int64_t>(1, kItemPoints / n)));
-        for (int64_t s = 0; s < poles; s += rpi) {
-            out.push_back(Item{g, phase, K_ROWS, 0, s, std::min(rpi, poles - s), -1, 0});
-            ++count;
-        }
-        return;
-    }
-    (void)es;
-    // long poles with few of them: one CTA sweeps a group level by level
-    const bool longp = gi.l[k] > 5 && (poles < 4 * kBThreads || k == 0);
-    if (longp) {
-        const int64_t ppi = std::max<int64_t>(1, kItemPoints * 4 / n);
-        for (int64_t s = 0; s < poles; s += ppi) {
-            out.push_back(Item{g, phase, K_LONG, k, s, std::min(ppi, poles - s), -1, 0});
-            ++count;
-        }
-        return;
-    }
-    const int64_t ppi = std::max<int64_t>(kBThreads, kItemPoints / n);
-    for (int64_t s = 0; s < poles; s += ppi) {
-        out.push_back(Item{g, phase, K_POLES, k, s, std::min(ppi, poles - s), -1, 0});
-        ++count;
-    }
-}
-
-int build_items(gbh_plan *p)
+int build_items(gbh_plan *p, int op, std::vector<Item> &items, std::vector<int> &need)
 {
     const int es = p->dtype == GBH_F64 ? 8 : 4;
-    p->need.assign((size_t)p->ngrids * kPhases, 0);
+    need.assign((size_t)p->ngrids * kPhases, 0);
+    items.clear();
     // waves of grids that fit in L2 together; phase-major inside a wave
     std::vector<int> order(p->ngrids);
     for (int g = 0; g < p->ngrids; ++g) order[g] = g;
@@ -628,15 +560,19 @@ int build_items(gbh_plan *p)
             ++w1;
         }
         std::vector<int> prev(w1 - w0, -1);          // last phase with items, per grid
-        for (int ph = (p->dtype == GBH_F64 ? 0 : 1); ph < kPhases; ++ph)
+        for (int ph = 0; ph < kPhases; ++ph)
             for (size_t w = w0; w < w1; ++w) {
                 const int g = order[w];
                 if (p->info[g].first_dim < 0) continue;
                 int cnt = 0;
-                const size_t first = p->items.size();
-                grid_items(p->info[g], g, p->d, es, ph, p->items, cnt);
-                for (size_t i = first; i < p->items.size(); ++i) p->items[i].wait = prev[w - w0];
-                p->need[(size_t)g * kPhases + ph] = cnt;
+                const int wait = prev[w - w0];
+                emit_items(p->info[g], p->d, p->dtype, op, ph, kItemPoints,
+                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
+                               items.push_back(Item{g, ph, kind, dim, st, c, wait, blk});
+                               ++cnt;
+                               return true;
+                           });
+                need[(size_t)g * kPhases + ph] = cnt;
                 if (cnt > 0) prev[w - w0] = ph;
             }
         w0 = w1;
@@ -658,7 +594,7 @@ int finish_plan(gbh_plan *p)
         double growth = 1.0;
         for (int k = 0; k < d; ++k) {
             const int l = p->levels[(size_t)g * d + k];
-            if (l < 0 || l > 30) return GBH_ERANGE;
+            if (l < 0 || l > kGroupLevel + 5) return GBH_ERANGE;
             gi.l[k] = l;
             gi.S[k] = N;
             const int64_t nk = ((int64_t)1 << l) + 1;
@@ -677,10 +613,12 @@ int finish_plan(gbh_plan *p)
         gi.g0_d = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
         p->total_points += N;
     }
-    if (int e = build_items(p)) return e;
+    for (int o = 0; o < 2; ++o) {
+        if (int e = build_items(p, o, p->items[o], p->need[o])) return e;
+        if (int e = upload(&p->d_items[o], p->items[o])) return e;
+        if (int e = upload(&p->d_need[o], p->need[o])) return e;
+    }
     if (int e = upload(&p->d_info, p->info)) return e;
-    if (int e = upload(&p->d_items, p->items)) return e;
-    if (int e = upload(&p->d_need, p->need)) return e;
     if (int e = upload(&p->d_coeffs, p->coeffs)) return e;
     if (cudaMalloc(reinterpret_cast<void **>(&p->d_ptrs), sizeof(void *) * p->ngrids) != cudaSuccess) return GBH_ENOMEM;
     p->scratch_bytes = 64 + sizeof(int) * (size_t)p->ngrids * (1 + kPhases);
@@ -887,18 +825,18 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     // queue, status and counters restart with every execution
     if (cudaMemsetAsync(plan->d_scratch, 0, plan->scratch_bytes, s) != cudaSuccess) return GBH_ECUDA;
     BatchParams P{};
-    P.items = plan->d_items;
-    P.nitems = (int)plan->items.size();
+    P.items = plan->d_items[op];
+    P.nitems = (int)plan->items[op].size();
     P.grids = plan->d_info;
     P.ptrs = plan->d_ptrs;
     P.ticket = reinterpret_cast<unsigned *>(plan->d_scratch);
     P.status = reinterpret_cast<int *>(plan->d_scratch + 32);
     P.emax = reinterpret_cast<int *>(plan->d_scratch + 64);
     P.done = P.emax + plan->ngrids;
-    P.need = plan->d_need;
+    P.need = plan->d_need[op];
     P.op = op;
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
-    const size_t smem = kRowsSmemElems * es;
+    const size_t smem = kGroupElems * es;
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
@@ -997,42 +935,6 @@ static unsigned char *g_na_dev[64];                // symbol address per device
 
 size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 
-// Items of grid g, phase ph (same decomposition as grid_items, larger items).
-bool na_items(const GridInfo &gi, int g, int d, int ph, int wait, int &nitems, int cap, int &cnt)
-{
-    cnt = 0;
-    auto push = [&](int kind, int dim, int64_t s, int64_t c) {
-        if (nitems >= cap) return false;
-        g_na_host.items[nitems++] = Item{g, ph, kind, dim, s, c, wait, 0};
-        ++cnt;
-        return true;
-    };
-    if (ph == 0) {
-        for (int64_t s = 0; s < gi.N; s += kNoAllocItemPoints)
-            if (!push(K_SCAN, 0, s, std::min<int64_t>(kNoAllocItemPoints, gi.N - s))) return false;
-        return true;
-    }
-    const int k = ph - 1;
-    if (k >= d || gi.l[k] == 0) return true;
-    const int64_t n = ((int64_t)1 << gi.l[k]) + 1, poles = gi.N / n;
-    if (k == 0 && n <= kRowsSmemElems) {
-        const int64_t rpi = std::max<int64_t>(1, kRowsSmemElems / n);
-        for (int64_t s = 0; s < poles; s += rpi)
-            if (!push(K_ROWS, 0, s, std::min(rpi, poles - s))) return false;
-        return true;
-    }
-    if (gi.l[k] > 5 && (poles < 4 * kBThreads || k == 0)) {
-        const int64_t ppi = std::max<int64_t>(1, kNoAllocItemPoints / n);
-        for (int64_t s = 0; s < poles; s += ppi)
-            if (!push(K_LONG, k, s, std::min(ppi, poles - s))) return false;
-        return true;
-    }
-    const int64_t ppi = std::max<int64_t>(kBThreads, kNoAllocItemPoints / n);
-    for (int64_t s = 0; s < poles; s += ppi)
-        if (!push(K_POLES, k, s, std::min(ppi, poles - s))) return false;
-    return true;
-}
-
 }  // namespace
 
 extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, void *const *grid_ptrs,
@@ -1054,7 +956,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
         double growth = 1.0;
         for (int k = 0; k < d; ++k) {
             const int l = levels[(size_t)g * d + k];
-            if (l < 0 || l > 30) return GBH_ERANGE;
+            if (l < 0 || l > kGroupLevel + 5) return GBH_ERANGE;
             const int64_t nk = ((int64_t)1 << l) + 1;
             if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
             gi.l[k] = l;
@@ -1098,12 +1000,20 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
             ++w1;
         }
         for (int w = w0; w < w1; ++w) prev[w] = -1;
-        for (int ph = (dtype == GBH_F64 ? 0 : 1); ph < kPhases; ++ph)
+        for (int ph = 0; ph < kPhases; ++ph)
             for (int w = w0; w < w1; ++w) {
                 const int g = g_na_host.order[w];
                 if (g_na_host.info[g].first_dim < 0) continue;
                 int cnt = 0;
-                if (!na_items(g_na_host.info[g], g, d, ph, prev[w], nitems, cap, cnt)) return GBH_ERANGE;
+                const int wait = prev[w];
+                const bool ok = emit_items(g_na_host.info[g], d, dtype, op, ph, kNoAllocItemPoints,
+                                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
+                                               if (nitems >= cap) return false;
+                                               g_na_host.items[nitems++] = Item{g, ph, kind, dim, st, c, wait, blk};
+                                               ++cnt;
+                                               return true;
+                                           });
+                if (!ok) return GBH_ERANGE;
                 g_na_host.need[g * kPhases + ph] = cnt;
                 if (cnt > 0) prev[w] = ph;
             }
@@ -1139,7 +1049,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
     P.need = reinterpret_cast<const int *>(base + o_need);
     P.op = op;
     if (nitems == 0) return GBH_OK;
-    const size_t smem = kRowsSmemElems * es;
+    const size_t smem = kGroupElems * es;
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;

@@ -49,6 +49,28 @@ def test_batched_transform(d, n, op, dtype):
         assert rel_err(g.cpu().double().numpy(), fn(u, l), u) <= tol, tuple(l)
 
 
+@pytest.mark.parametrize("op", [gbh.GBH_HIERARCHIZE, gbh.GBH_DEHIERARCHIZE])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_long_dimensions(op, dtype):
+    """Levels 6..17: shared-memory pole groups, and above 12 the block /
+    coarse-lattice split."""
+    levels = np.array([[14, 1], [1, 14], [13, 2, 1], [1, 2, 16], [17, 1], [6, 7], [8, 1, 9],
+                       [12, 1], [1, 12], [3, 13]], dtype=object)
+    levels = [np.array(l, dtype=np.int32) for l in levels]
+    for lv_group in ([l for l in levels if len(l) == 2], [l for l in levels if len(l) == 3]):
+        lv = np.stack(lv_group)
+        plan = gbh.Plan.from_levels(lv, dtype=str(dtype))
+        grids = _grids(lv, dtype)
+        host = [g.cpu().double().numpy() for g in grids]
+        plan.bind(grids)
+        plan.execute(op)
+        assert plan.status() == 0
+        fn = oracle.hierarchize if op == gbh.GBH_HIERARCHIZE else oracle.dehierarchize
+        tol = 1e-13 if dtype == torch.float64 else 1e-5
+        for l, g, u in zip(lv, grids, host):
+            assert rel_err(g.cpu().double().numpy(), fn(u, l), u) <= tol, tuple(l)
+
+
 def test_batched_round_trip_twice():
     plan = gbh.Plan.scheme(3, 6)
     grids = _grids(plan.levels(), torch.float64)
