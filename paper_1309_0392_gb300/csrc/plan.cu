@@ -36,15 +36,33 @@ constexpr long long kSpinLimit = 1ll << 24;   // bounded waits (~ seconds)
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
 enum ItemKind { K_SCAN = 0, K_CONV_IN = 1, K_CONV_OUT = 2, K_ROWS = 3, K_POLES = 4, K_GROUP = 5, K_LATT = 6 };
 
+// t / S as __umul64hi(t, ceil(2^64 / S)), exact for t < 2^64 / S; S = 1 is
+// marked by m = 0.
+struct FastDiv {
+    unsigned long long m;
+};
+__host__ inline FastDiv make_fastdiv(int64_t S)
+{
+    FastDiv f;
+    f.m = S == 1 ? 0ull : (~0ull / (unsigned long long)S) + 1ull;
+    return f;
+}
+__device__ __forceinline__ int64_t fdiv(int64_t t, FastDiv f)
+{
+    return f.m ? (int64_t)__umul64hi((unsigned long long)t, f.m) : t;
+}
+
 struct GridInfo {
     int l[kPlanMaxD];
     int64_t S[kPlanMaxD];
+    FastDiv divS[kPlanMaxD];
     int64_t N;
     int first_dim;       // first and last dimension with a sweep (-1: none)
     int last_dim;
     int g0;              // fixed point: input scale bits (per op)
     int g0_d;
     int passes;          // dimensions with a sweep
+    int pad;
 };
 
 struct Item {
@@ -67,7 +85,29 @@ __device__ __forceinline__ int ld_acquire(const int *p)
 
 // fp64 <-> fixed point (see fused.cu for the derivation): the grid's largest
 // magnitude sits just below 2^{g0}.
-__device__ __forceinline__ long long b_to_fixed(double x, int emax, int c)
+__device__ __noinline__ long long b_to_fixed_slow(double x, int emax, int c);
+__device__ __noinline__ double b_from_fixed_slow(long long v, int X);
+
+// Fast forms for grids whose largest exponent lies in [64, 1900]: zeros and
+// subnormals fall out of the shift, every nonzero result is a normal number.
+__device__ __forceinline__ long long b_to_fixed_fast(double x, int emax, int c)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7FF);
+    const unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int P = c > 0 ? c : 0;
+    int rs = emax - e + P - c;
+    rs = rs > 63 ? 63 : rs;
+    const long long v = (long long)((M << P) >> rs);
+    return bits < 0 ? -v : v;
+}
+__device__ __forceinline__ double b_from_fixed_fast(long long v, int X)
+{
+    const long long b = __double_as_longlong(__ll2double_rn(v));
+    return __longlong_as_double(v == 0 ? 0ll : b + ((long long)X << 52));
+}
+
+__device__ __noinline__ long long b_to_fixed_slow(double x, int emax, int c)
 {
     const long long bits = __double_as_longlong(x);
     const int e = (int)((bits >> 52) & 0x7FF);
@@ -80,7 +120,7 @@ __device__ __forceinline__ long long b_to_fixed(double x, int emax, int c)
     return bits < 0 ? -v : v;
 }
 
-__device__ __forceinline__ double b_from_fixed(long long v, int X)
+__device__ __noinline__ double b_from_fixed_slow(long long v, int X)
 {
     if (v == 0) return 0.0;
     const double r = __ll2double_rn(v);
@@ -178,11 +218,12 @@ __device__ __forceinline__ void b_rows_regs(V *sv, int rows)
 // `st` from there (a coarse lattice uses st = 2^m S).  One thread per pole,
 // loads and stores all independent.
 template <typename V, int L, int OP>
-__device__ __forceinline__ void b_poles_regs(V *base, int64_t S, int64_t n, int64_t st, int64_t start, int64_t count)
+__device__ __forceinline__ void b_poles_regs(V *base, int64_t S, FastDiv dS, int64_t n, int64_t st, int64_t start,
+                                             int64_t count)
 {
     constexpr int np = (1 << L) + 1;
     for (int64_t t = start + threadIdx.x; t < start + count; t += blockDim.x) {
-        const int64_t o = t / S, j = t - o * S;
+        const int64_t o = fdiv(t, dS), j = t - o * S;
         V *pp = base + o * S * n + j;
         V v[np];
 #pragma unroll
@@ -194,15 +235,15 @@ __device__ __forceinline__ void b_poles_regs(V *base, int64_t S, int64_t n, int6
 }
 
 template <typename V, int OP>
-__device__ __forceinline__ void b_poles_dispatch(int L, V *base, int64_t S, int64_t n, int64_t st, int64_t start,
-                                                 int64_t count)
+__device__ __forceinline__ void b_poles_dispatch(int L, V *base, int64_t S, FastDiv dS, int64_t n, int64_t st,
+                                                 int64_t start, int64_t count)
 {
     switch (L) {
-        case 1: b_poles_regs<V, 1, OP>(base, S, n, st, start, count); break;
-        case 2: b_poles_regs<V, 2, OP>(base, S, n, st, start, count); break;
-        case 3: b_poles_regs<V, 3, OP>(base, S, n, st, start, count); break;
-        case 4: b_poles_regs<V, 4, OP>(base, S, n, st, start, count); break;
-        case 5: b_poles_regs<V, 5, OP>(base, S, n, st, start, count); break;
+        case 1: b_poles_regs<V, 1, OP>(base, S, dS, n, st, start, count); break;
+        case 2: b_poles_regs<V, 2, OP>(base, S, dS, n, st, start, count); break;
+        case 3: b_poles_regs<V, 3, OP>(base, S, dS, n, st, start, count); break;
+        case 4: b_poles_regs<V, 4, OP>(base, S, dS, n, st, start, count); break;
+        case 5: b_poles_regs<V, 5, OP>(base, S, dS, n, st, start, count); break;
         default: break;
     }
 }
@@ -296,10 +337,19 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                 const int c = (OP == OP_H ? gi.g0 : gi.g0_d) - 53;
                 const int X = emax - 1075 - c - (OP == OP_H ? gi.passes : 0);
                 long long *b = reinterpret_cast<long long *>(sbase);
-                for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
-                    const long long v = __ldcg(b + i);
-                    __stcg(b + i, it.kind == K_CONV_IN ? b_to_fixed(__longlong_as_double(v), emax, c)
-                                                       : __double_as_longlong(b_from_fixed(v, X)));
+                const bool fast = emax >= 64 && emax <= 1900;
+                if (fast && it.kind == K_CONV_IN) {
+                    for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x)
+                        __stcg(b + i, b_to_fixed_fast(__longlong_as_double(__ldcg(b + i)), emax, c));
+                } else if (fast) {
+                    for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x)
+                        __stcg(b + i, __double_as_longlong(b_from_fixed_fast(__ldcg(b + i), X)));
+                } else {
+                    for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
+                        const long long v = __ldcg(b + i);
+                        __stcg(b + i, it.kind == K_CONV_IN ? b_to_fixed_slow(__longlong_as_double(v), emax, c)
+                                                           : __double_as_longlong(b_from_fixed_slow(v, X)));
+                    }
                 }
             }
         } else {
@@ -322,11 +372,11 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                 }
                 for (int e = tid; e < cnt; e += blockDim.x) __stcg(base + e0 + e, sv[e]);
             } else if (it.kind == K_POLES) {
-                b_poles_dispatch<V, OP>(l, base, S, n, S, it.start, it.count);
+                b_poles_dispatch<V, OP>(l, base, S, gi.divS[k], n, S, it.start, it.count);
             } else if (it.kind == K_LATT) {
                 // coarse lattice of a long dimension: points a 2^m, stride 2^m S
                 const int m = l < kGroupLevel ? l : kGroupLevel;
-                b_poles_dispatch<V, OP>(l - m, base, S, n, S << m, it.start, it.count);
+                b_poles_dispatch<V, OP>(l - m, base, S, gi.divS[k], n, S << m, it.start, it.count);
             } else {
                 // K_GROUP: block `blk` (2^m + 1 points) of `count` poles in
                 // shared memory; a block covering the whole pole writes it
@@ -334,19 +384,24 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                 const int m = l < kGroupLevel ? l : kGroupLevel;
                 const int nb = (1 << m) + 1;
                 const int G = (int)it.count;
+                const unsigned magG = G == 1 ? 0u : (0xFFFFFFFFu / (unsigned)G) + 1u;
                 const int64_t off0 = (int64_t)it.blk << m;
+                int64_t *pb = reinterpret_cast<int64_t *>(sm + (size_t)kGroupElems * sizeof(V));
+                for (int g = tid; g < G; g += blockDim.x) {
+                    const int64_t t = it.start + g, o = fdiv(t, gi.divS[k]);
+                    pb[g] = o * S * n + (t - o * S) + off0 * S;
+                }
+                __syncthreads();
                 for (int w = tid; w < G * nb; w += blockDim.x) {
-                    const int g = w % G, i = w / G;
-                    const int64_t t = it.start + g, o = t / S;
-                    sv[g * nb + i] = __ldcg(base + o * S * n + (t - o * S) + (off0 + i) * S);
+                    const int i = magG ? (int)__umulhi((unsigned)w, magG) : w, g = w - i * G;
+                    sv[g * nb + i] = __ldcg(base + pb[g] + (int64_t)i * S);
                 }
                 __syncthreads();
                 b_smem_sweep<V, OP>(sv, G, nb, m, m == l);
                 const int lo = m == l ? 0 : 1, hi = m == l ? nb : nb - 1;
                 for (int w = tid; w < G * (hi - lo); w += blockDim.x) {
-                    const int g = w % G, i = lo + w / G;
-                    const int64_t t = it.start + g, o = t / S;
-                    __stcg(base + o * S * n + (t - o * S) + (off0 + i) * S, sv[g * nb + i]);
+                    const int q = magG ? (int)__umulhi((unsigned)w, magG) : w, g = w - q * G, i = lo + q;
+                    __stcg(base + pb[g] + (int64_t)i * S, sv[g * nb + i]);
                 }
             }
         }
@@ -597,6 +652,7 @@ int finish_plan(gbh_plan *p)
             if (l < 0 || l > kGroupLevel + 5) return GBH_ERANGE;
             gi.l[k] = l;
             gi.S[k] = N;
+            gi.divS[k] = make_fastdiv(N);
             const int64_t nk = ((int64_t)1 << l) + 1;
             if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
             N *= nk;
@@ -836,7 +892,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.need = plan->d_need[op];
     P.op = op;
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
-    const size_t smem = kGroupElems * es;
+    const size_t smem = kGroupElems * es + kGroupElems * sizeof(int64_t) / 2;
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
@@ -961,6 +1017,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
             if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
             gi.l[k] = l;
             gi.S[k] = N;
+            gi.divS[k] = make_fastdiv(N);
             N *= nk;
             if (l > 0) {
                 if (gi.first_dim < 0) gi.first_dim = k;
@@ -1049,7 +1106,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
     P.need = reinterpret_cast<const int *>(base + o_need);
     P.op = op;
     if (nitems == 0) return GBH_OK;
-    const size_t smem = kGroupElems * es;
+    const size_t smem = kGroupElems * es + kGroupElems * sizeof(int64_t) / 2;
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
