@@ -287,6 +287,27 @@ __device__ __forceinline__ void b_smem_sweep(V *sv, int rows, int pitch, int L, 
     }
 }
 
+// Streams `count` elements: src(e) -> dst(e, value), with up to kU loads in
+// flight per thread (all loads of a group issue before its stores).
+constexpr int kU = 8;
+template <typename T, typename Src, typename Dst>
+__device__ __forceinline__ void stream_elems(int64_t count, Src src, Dst dst)
+{
+    for (int64_t e0 = threadIdx.x; e0 < count; e0 += (int64_t)blockDim.x * kU) {
+        T tmp[kU];
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+            const int64_t e = e0 + (int64_t)q * blockDim.x;
+            if (e < count) tmp[q] = src(e);
+        }
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+            const int64_t e = e0 + (int64_t)q * blockDim.x;
+            if (e < count) dst(e, tmp[q]);
+        }
+    }
+}
+
 template <typename ST, int OP>
 __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
 {
@@ -324,11 +345,12 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
 
         if (it.kind == K_SCAN) {
             int em = 0;
-            const long long *b = reinterpret_cast<const long long *>(sbase);
-            for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
-                const int e = (int)((__ldcg(b + i) >> 52) & 0x7FF);
-                em = e > em ? e : em;
-            }
+            const long long *b = reinterpret_cast<const long long *>(sbase) + it.start;
+            stream_elems<long long>(it.count, [&](int64_t e) { return __ldcg(b + e); },
+                                    [&](int64_t, long long v) {
+                                        const int ex = (int)((v >> 52) & 0x7FF);
+                                        em = ex > em ? ex : em;
+                                    });
             em = __reduce_max_sync(0xFFFFFFFFu, (unsigned)em);
             if ((tid & 31) == 0 && em > 0) atomicMax(P.emax + it.grid, em);
         } else if (it.kind == K_CONV_IN || it.kind == K_CONV_OUT) {
@@ -338,12 +360,17 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                 const int X = emax - 1075 - c - (OP == OP_H ? gi.passes : 0);
                 long long *b = reinterpret_cast<long long *>(sbase);
                 const bool fast = emax >= 64 && emax <= 1900;
+                long long *bb = b + it.start;
                 if (fast && it.kind == K_CONV_IN) {
-                    for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x)
-                        __stcg(b + i, b_to_fixed_fast(__longlong_as_double(__ldcg(b + i)), emax, c));
+                    stream_elems<long long>(it.count, [&](int64_t e) { return __ldcg(bb + e); },
+                                            [&](int64_t e, long long v) {
+                                                __stcg(bb + e, b_to_fixed_fast(__longlong_as_double(v), emax, c));
+                                            });
                 } else if (fast) {
-                    for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x)
-                        __stcg(b + i, __double_as_longlong(b_from_fixed_fast(__ldcg(b + i), X)));
+                    stream_elems<long long>(it.count, [&](int64_t e) { return __ldcg(bb + e); },
+                                            [&](int64_t e, long long v) {
+                                                __stcg(bb + e, __double_as_longlong(b_from_fixed_fast(v, X)));
+                                            });
                 } else {
                     for (int64_t i = it.start + tid; i < it.start + it.count; i += blockDim.x) {
                         const long long v = __ldcg(b + i);
@@ -359,7 +386,8 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                 // dimension 0: `count` whole rows staged in shared memory
                 const int64_t e0 = it.start * n;
                 const int cnt = (int)(it.count * n);
-                for (int e = tid; e < cnt; e += blockDim.x) sv[e] = __ldcg(base + e0 + e);
+                V *src = base + e0;
+                stream_elems<V>(cnt, [&](int64_t e) { return __ldcg(src + e); }, [&](int64_t e, V v) { sv[e] = v; });
                 __syncthreads();
                 const int rows = (int)it.count;
                 switch (l) {
@@ -370,7 +398,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                     case 5: b_rows_regs<V, 5, OP>(sv, rows); __syncthreads(); break;
                     default: b_smem_sweep<V, OP>(sv, rows, (int)n, l, true); break;
                 }
-                for (int e = tid; e < cnt; e += blockDim.x) __stcg(base + e0 + e, sv[e]);
+                stream_elems<V>(cnt, [&](int64_t e) { return sv[e]; }, [&](int64_t e, V v) { __stcg(src + e, v); });
             } else if (it.kind == K_POLES) {
                 b_poles_dispatch<V, OP>(l, base, S, gi.divS[k], n, S, it.start, it.count);
             } else if (it.kind == K_LATT) {
@@ -392,10 +420,16 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                     pb[g] = o * S * n + (t - o * S) + off0 * S;
                 }
                 __syncthreads();
-                for (int w = tid; w < G * nb; w += blockDim.x) {
-                    const int i = magG ? (int)__umulhi((unsigned)w, magG) : w, g = w - i * G;
-                    sv[g * nb + i] = __ldcg(base + pb[g] + (int64_t)i * S);
-                }
+                stream_elems<V>(
+                    (int64_t)G * nb,
+                    [&](int64_t w) {
+                        const int i = magG ? (int)__umulhi((unsigned)w, magG) : (int)w, g = (int)w - i * G;
+                        return __ldcg(base + pb[g] + (int64_t)i * S);
+                    },
+                    [&](int64_t w, V v) {
+                        const int i = magG ? (int)__umulhi((unsigned)w, magG) : (int)w, g = (int)w - i * G;
+                        sv[g * nb + i] = v;
+                    });
                 __syncthreads();
                 b_smem_sweep<V, OP>(sv, G, nb, m, m == l);
                 const int lo = m == l ? 0 : 1, hi = m == l ? nb : nb - 1;
