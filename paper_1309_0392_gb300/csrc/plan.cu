@@ -30,7 +30,7 @@ namespace {
 constexpr int kPlanMaxD = 8;
 constexpr int kBThreads = 256;
 constexpr int64_t kItemPoints = 32768;        // target points per item
-constexpr double kWaveBytes = 48.0 * 1024 * 1024;
+constexpr double kWaveBytes = 16.0 * 1024 * 1024;
 constexpr long long kSpinLimit = 1ll << 24;   // bounded waits (~ seconds)
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
@@ -148,7 +148,6 @@ struct BatchParams {
 // block part and a coarse-lattice part), then the conversion back.
 constexpr int kPhases = 3 + 2 * kPlanMaxD;
 constexpr int kPhaseOut = kPhases - 1;
-__host__ __device__ constexpr int dim_phase(int k, int sub) { return 2 + 2 * k + sub; }
 constexpr int kGroupLevel = 12;                  // block level of long dimensions
 constexpr int kGroupElems = 8208;               // shared-memory elements per item
 
@@ -631,41 +630,71 @@ int upload(T **dst, const std::vector<T> &src)
     return GBH_OK;
 }
 
+// Ticket order: grids (largest first) are cut into waves of about kWaveBytes;
+// items are issued along diagonals of (wave, phase): all items with
+// wave + phase = t, then t + 1, ...  An item's dependency (the previous phase of
+// its grid) lies on an earlier diagonal, so consecutive tickets are
+// independent while a few waves stay resident in L2.
+template <typename Push>
+bool order_items(const GridInfo *info, int ngrids, int d, int dtype, int op, int64_t chunk, double wave_bytes,
+                 int *order, int *wave_of, int *prev, int *need, Push push)
+{
+    const int es = dtype == GBH_F64 ? 8 : 4;
+    for (int g = 0; g < ngrids; ++g) order[g] = g;
+    std::sort(order, order + ngrids, [&](int a, int b) { return info[a].N > info[b].N || (info[a].N == info[b].N && a < b); });
+    int nwaves = 0;
+    {
+        int w0 = 0;
+        while (w0 < ngrids) {
+            int w1 = w0;
+            double bytes = 0.0;
+            while (w1 < ngrids && (w1 == w0 || bytes + (double)info[order[w1]].N * es <= wave_bytes)) {
+                bytes += (double)info[order[w1]].N * es;
+                wave_of[w1] = nwaves;
+                ++w1;
+            }
+            ++nwaves;
+            w0 = w1;
+        }
+    }
+    for (int i = 0; i < ngrids; ++i) prev[i] = -1;
+    for (int i = 0; i < ngrids * kPhases; ++i) need[i] = 0;
+    for (int t = 0; t < nwaves + kPhases - 1; ++t) {
+        int gi0 = 0;
+        for (int w = 0; w < nwaves; ++w) {
+            while (gi0 < ngrids && wave_of[gi0] < w) ++gi0;
+            const int ph = t - w;
+            if (ph < 0 || ph >= kPhases) continue;
+            for (int i = gi0; i < ngrids && wave_of[i] == w; ++i) {
+                const int g = order[i];
+                if (info[g].first_dim < 0) continue;
+                int cnt = 0;
+                const int wait = prev[i];
+                const bool ok = emit_items(info[g], d, dtype, op, ph, chunk,
+                                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
+                                               if (!push(Item{g, ph, kind, dim, st, c, wait, blk})) return false;
+                                               ++cnt;
+                                               return true;
+                                           });
+                if (!ok) return false;
+                need[(size_t)g * kPhases + ph] = cnt;
+                if (cnt > 0) prev[i] = ph;
+            }
+        }
+    }
+    return true;
+}
+
 int build_items(gbh_plan *p, int op, std::vector<Item> &items, std::vector<int> &need)
 {
-    const int es = p->dtype == GBH_F64 ? 8 : 4;
     need.assign((size_t)p->ngrids * kPhases, 0);
     items.clear();
-    // waves of grids that fit in L2 together; phase-major inside a wave
-    std::vector<int> order(p->ngrids);
-    for (int g = 0; g < p->ngrids; ++g) order[g] = g;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->info[a].N > p->info[b].N; });
-    size_t w0 = 0;
-    while (w0 < order.size()) {
-        size_t w1 = w0;
-        double bytes = 0.0;
-        while (w1 < order.size() && (w1 == w0 || bytes + (double)p->info[order[w1]].N * es <= kWaveBytes)) {
-            bytes += (double)p->info[order[w1]].N * es;
-            ++w1;
-        }
-        std::vector<int> prev(w1 - w0, -1);          // last phase with items, per grid
-        for (int ph = 0; ph < kPhases; ++ph)
-            for (size_t w = w0; w < w1; ++w) {
-                const int g = order[w];
-                if (p->info[g].first_dim < 0) continue;
-                int cnt = 0;
-                const int wait = prev[w - w0];
-                emit_items(p->info[g], p->d, p->dtype, op, ph, kItemPoints,
-                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
-                               items.push_back(Item{g, ph, kind, dim, st, c, wait, blk});
-                               ++cnt;
-                               return true;
-                           });
-                need[(size_t)g * kPhases + ph] = cnt;
-                if (cnt > 0) prev[w - w0] = ph;
-            }
-        w0 = w1;
-    }
+    std::vector<int> order(p->ngrids), wave(p->ngrids), prev(p->ngrids);
+    order_items(p->info.data(), p->ngrids, p->d, p->dtype, op, kItemPoints, kWaveBytes, order.data(), wave.data(),
+                prev.data(), need.data(), [&](const Item &it) {
+                    items.push_back(it);
+                    return true;
+                });
     return GBH_OK;
 }
 
@@ -1076,40 +1105,16 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
     if (o_items >= kNoAllocBytes) return GBH_ERANGE;
     const int cap = (int)std::min<size_t>((kNoAllocBytes - o_items) / sizeof(Item),
                                           sizeof(g_na_host.items) / sizeof(Item));
-    // items: waves of grids that fit in L2 together, phase-major inside a wave
-    std::sort(g_na_host.order, g_na_host.order + n_grids,
-              [](int a, int b) { return g_na_host.info[a].N > g_na_host.info[b].N || (g_na_host.info[a].N == g_na_host.info[b].N && a < b); });
-    std::memset(g_na_host.need, 0, sizeof(int) * (size_t)n_grids * kPhases);
+    // items in the plan's ticket order
     int nitems = 0;
-    int w0 = 0;
-    int prev[kNoAllocMaxGrids];
-    while (w0 < n_grids) {
-        int w1 = w0;
-        double bytes = 0.0;
-        while (w1 < n_grids && (w1 == w0 || bytes + (double)g_na_host.info[g_na_host.order[w1]].N * es <= kWaveBytes)) {
-            bytes += (double)g_na_host.info[g_na_host.order[w1]].N * es;
-            ++w1;
-        }
-        for (int w = w0; w < w1; ++w) prev[w] = -1;
-        for (int ph = 0; ph < kPhases; ++ph)
-            for (int w = w0; w < w1; ++w) {
-                const int g = g_na_host.order[w];
-                if (g_na_host.info[g].first_dim < 0) continue;
-                int cnt = 0;
-                const int wait = prev[w];
-                const bool ok = emit_items(g_na_host.info[g], d, dtype, op, ph, kNoAllocItemPoints,
-                                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
-                                               if (nitems >= cap) return false;
-                                               g_na_host.items[nitems++] = Item{g, ph, kind, dim, st, c, wait, blk};
-                                               ++cnt;
-                                               return true;
-                                           });
-                if (!ok) return GBH_ERANGE;
-                g_na_host.need[g * kPhases + ph] = cnt;
-                if (cnt > 0) prev[w] = ph;
-            }
-        w0 = w1;
-    }
+    static int na_wave[kNoAllocMaxGrids], na_prev[kNoAllocMaxGrids];
+    const bool ok = order_items(g_na_host.info, n_grids, d, dtype, op, kNoAllocItemPoints, kWaveBytes,
+                                g_na_host.order, na_wave, na_prev, g_na_host.need, [&](const Item &it) {
+                                    if (nitems >= cap) return false;
+                                    g_na_host.items[nitems++] = it;
+                                    return true;
+                                });
+    if (!ok) return GBH_ERANGE;
     // set-up: the array's device address, once per device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GBH_ECUDA;
