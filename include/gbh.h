@@ -171,6 +171,10 @@ int gbh_plan_num_grids(const gbh_plan *plan, int *out);
 int gbh_plan_grid_levels(const gbh_plan *plan, int g, int32_t *levels_out);
 /* Combination coefficients of all grids (n_grids doubles) into coeffs_out. */
 int gbh_plan_coeffs(const gbh_plan *plan, double *coeffs_out);
+/* Replace the combination coefficients (host array of n_grids doubles; copied
+ * synchronously).  A coefficient of 0 leaves that grid out of the gather, which
+ * is how a rank gathers only the grids it owns. */
+int gbh_plan_set_coeffs(gbh_plan *plan, const double *coeffs);
 /* Points of the sparse grid (scheme plans), total grid points (all plans). */
 int gbh_plan_sparse_points(const gbh_plan *plan, int64_t *out);
 int gbh_plan_total_points(const gbh_plan *plan, int64_t *out);
@@ -222,6 +226,16 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream);
  */
 int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, void *const *grid_ptrs,
                                   int dtype, int op, void *stream);
+
+/*
+ * Failure injection for tests.  With grid >= 0, the next executions of the plan
+ * make every work item of that grid wait for a dependency that is never
+ * released; the bounded waits give up after `spin_limit` polls, record
+ * GBH_ETIMEOUT in the plan's status word and the kernel returns (the grids'
+ * contents are then unspecified).  grid = -1 restores normal operation.  No
+ * GPU fault, trap or hang is involved.
+ */
+int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit);
 
 /* Sticky device-side status of a plan (GBH_ETIMEOUT after an expired wait);
  * synchronises the stream given.  Reading it clears it. */

@@ -56,12 +56,14 @@ _SIGS = {
     "gbh_plan_num_grids": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "gbh_plan_grid_levels": (ctypes.c_int, [_VP, ctypes.c_int, _I32P]),
     "gbh_plan_coeffs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "gbh_plan_set_coeffs": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "gbh_plan_sparse_points": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "gbh_plan_total_points": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "gbh_plan_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), _VP]),
     "gbh_plan_execute": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "gbh_plan_gather": (ctypes.c_int, [_VP, _VP, _VP]),
     "gbh_plan_status": (ctypes.c_int, [_VP, _VP]),
+    "gbh_plan_test_stall": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
     "gbh_batched_transform_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P, ctypes.POINTER(_VP),
                                                      ctypes.c_int, ctypes.c_int, _VP]),
     "gbh_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -141,6 +141,7 @@ struct BatchParams {
     unsigned *ticket;
     int *status;
     int op;
+    long long spin_limit;   // bounded waits: polls before giving up
 };
 
 // Phases of a grid: 0 exponent scan and 1 conversion to fixed point (fp64
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
                     const int want = P.need[it.grid * kPhases + it.wait];
                     long long spins = 0;
                     while (ld_acquire(cnt) < want) {
-                        if (++spins > kSpinLimit) { atomicExch(P.status, GBH_ETIMEOUT); s_abort = 1; break; }
+                        if (++spins > P.spin_limit) { atomicExch(P.status, GBH_ETIMEOUT); s_abort = 1; break; }
                         __nanosleep(64);
                     }
                 }
@@ -597,6 +598,8 @@ struct gbh_plan {
     void **h_ptrs = nullptr;          // pinned staging for bind
     bool bound = false;
     int dev = 0;
+    int stall_grid = -1;              // test hook: a dependency nothing releases
+    long long spin_limit = kSpinLimit;
 };
 
 namespace {
@@ -901,6 +904,15 @@ int gbh_plan_coeffs(const gbh_plan *plan, double *coeffs_out)
     return GBH_OK;
 }
 
+int gbh_plan_set_coeffs(gbh_plan *plan, const double *coeffs)
+{
+    if (!plan || !coeffs) return GBH_EINVAL;
+    std::memcpy(plan->coeffs.data(), coeffs, sizeof(double) * plan->ngrids);
+    if (cudaMemcpy(plan->d_coeffs, coeffs, sizeof(double) * plan->ngrids, cudaMemcpyHostToDevice) != cudaSuccess)
+        return GBH_ECUDA;
+    return GBH_OK;
+}
+
 int gbh_plan_sparse_points(const gbh_plan *plan, int64_t *out)
 {
     if (!plan || !out) return GBH_EINVAL;
@@ -954,6 +966,16 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.done = P.emax + plan->ngrids;
     P.need = plan->d_need[op];
     P.op = op;
+    P.spin_limit = plan->spin_limit;
+    if (plan->stall_grid >= 0) {
+        // every phase of the chosen grid waits for one item more than exists
+        std::vector<int> need = plan->need[op];
+        for (int ph = 0; ph < kPhases; ++ph) need[(size_t)plan->stall_grid * kPhases + ph] += 1;
+        if (cudaMemcpyAsync(plan->d_need[op], need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return GBH_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
+    }
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
     const size_t smem = kGroupElems * es + kGroupElems * sizeof(int64_t) / 2;
     auto launch = [&](auto kern) -> int {
@@ -1000,6 +1022,21 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
     ps.done();
     count_launches(1);
     return check_launch();
+}
+
+int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit)
+{
+    if (!plan || grid < -1 || grid >= plan->ngrids || spin_limit < 1) return GBH_EINVAL;
+    plan->stall_grid = grid;
+    plan->spin_limit = grid < 0 ? kSpinLimit : spin_limit;
+    if (grid < 0) {
+        // restore the real item counts
+        for (int o = 0; o < 2; ++o)
+            if (cudaMemcpy(plan->d_need[o], plan->need[o].data(), plan->need[o].size() * sizeof(int),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
+                return GBH_ECUDA;
+    }
+    return GBH_OK;
 }
 
 int gbh_plan_status(gbh_plan *plan, void *stream)
@@ -1134,6 +1171,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
         cudaMemcpyAsync(base + o_items, g_na_host.items, sizeof(Item) * (size_t)nitems, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return GBH_ECUDA;
     BatchParams P{};
+    P.spin_limit = kSpinLimit;
     P.items = reinterpret_cast<const Item *>(base + o_items);
     P.nitems = nitems;
     P.grids = reinterpret_cast<const GridInfo *>(base + o_info);

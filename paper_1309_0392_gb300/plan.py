@@ -65,6 +65,13 @@ class Plan:
                    "gbh_plan_coeffs")
         return out
 
+    def set_coeffs(self, coeffs):
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        if c.shape != (self.num_grids,):
+            raise ValueError("one coefficient per grid")
+        _lib.check(_lib.lib().gbh_plan_set_coeffs(self._h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                   "gbh_plan_set_coeffs")
+
     @property
     def sparse_points(self) -> int:
         v = ctypes.c_int64(0)
@@ -97,6 +104,11 @@ class Plan:
         _lib.check(_lib.lib().gbh_plan_gather(self._h, ctypes.c_void_p(sparse.data_ptr()),
                                               ctypes.c_void_p(s.cuda_stream)), "gbh_plan_gather")
         return sparse
+
+    def test_stall(self, grid: int, spin_limit: int = 1 << 14):
+        """Failure injection: the grid's work items wait on a dependency that
+        is never released (grid=-1 restores normal operation)."""
+        _lib.check(_lib.lib().gbh_plan_test_stall(self._h, int(grid), int(spin_limit)), "gbh_plan_test_stall")
 
     def status(self, stream=None) -> int:
         import torch

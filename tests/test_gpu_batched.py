@@ -158,3 +158,24 @@ def test_full_scheme_d4_n14_sampled():
     assert plan.status() == 0
     for g in picks:
         assert rel_err(grids[g].cpu().numpy(), oracle.hierarchize(host[g], lv[g]), host[g]) <= 1e-13
+
+
+def test_bounded_wait_reports_timeout():
+    """A dependency that nothing releases: the waits give up, the plan reports
+    GBH_ETIMEOUT, the context stays usable, and normal operation resumes."""
+    plan = gbh.Plan.scheme(3, 5)
+    lv = plan.levels()
+    grids = _grids(lv, torch.float64)
+    plan.bind(grids)
+    plan.test_stall(3, spin_limit=1 << 12)
+    plan.execute(gbh.GBH_HIERARCHIZE)
+    assert plan.status() == -6
+    assert plan.status() == 0                       # reading clears it
+    plan.test_stall(-1)
+    fresh = _grids(lv, torch.float64)
+    host = [g.cpu().numpy() for g in fresh]
+    plan.bind(fresh)
+    plan.execute(gbh.GBH_HIERARCHIZE)
+    assert plan.status() == 0
+    for l, g, u in zip(lv, fresh, host):
+        assert rel_err(g.cpu().numpy(), oracle.hierarchize(u, l), u) <= 1e-13
