@@ -456,7 +456,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", action="store_true")
+    ap.add_argument("--forms", action="store_true", default=True)
+    ap.add_argument("--no-forms", dest="forms", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
