@@ -160,6 +160,23 @@ def time_region(fn, steps, stream):
     return e0.elapsed_time(e1)
 
 
+def committed_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/traffic.json), or None if absent or if the kernel's source has
+    changed since the capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        src = os.path.join(ROOT, rec["source"])
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
+                return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def dominant_kernel(prof):
     """(name, launches, avg_ms, alg_bytes_per_launch) of the kernel with the
     largest total device time."""
@@ -411,12 +428,13 @@ def run_ours(args):
     e2e_val = 2.0 * N * world / (ms_e2e * 1e-3) / 1e9
 
     dom = dominant_kernel(prof)
+    traffic = committed_traffic(dom[0] if dom else None)
     roof = None
     if dom is not None:
         name, n, avg_ms, by = dom
         achieved = by / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": f"{peak_kind} (burst copy)", "traffic": None,
+                "frac": achieved / hbm, "peak_kind": f"{peak_kind} (burst copy)", "traffic": traffic,
                 "alg_bytes_per_launch": by, "avg_launch_ms": avg_ms, "launches": n}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -450,17 +468,50 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """One small workload for profilers: `transform:L0,L1,..:op:dtype` or
+    `scheme:d,n:op:dtype` (op h/d/a, dtype f64/f32), run warmup + steps times;
+    prints one JSON line with the median time."""
+    import torch
+
+    import paper_1309_0392_gb300 as gbh
+    kind, spec, op, dt = args.case.split(":")
+    dtype = torch.float64 if dt == "f64" else torch.float32
+    opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}[op]
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    if kind == "transform":
+        levels = tuple(int(v) for v in spec.split(","))
+        t = torch.empty(gbh.num_points(levels), dtype=dtype, device="cuda").uniform_(-1, 1, generator=gen)
+        fn = lambda: gbh.transform(t, levels, opc)  # noqa: E731
+        pts = t.numel()
+    else:
+        d, n = (int(v) for v in spec.split(","))
+        plan = gbh.Plan.scheme(d, n, dtype=str(dtype))
+        grids = [torch.empty(gbh.num_points(l), dtype=dtype, device="cuda").uniform_(-1, 1, generator=gen)
+                 for l in plan.levels()]
+        plan.bind(grids)
+        fn = lambda: plan.execute(opc)  # noqa: E731
+        pts = plan.total_points
+    for _ in range(args.warmup):
+        fn()
+    ms = _ms(fn, max(1, args.steps))
+    print(json.dumps({"case": args.case, "ms": ms, "points": pts, "Gpts_s": pts / (ms * 1e-3) / 1e9}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", action="store_true", default=True)
     ap.add_argument("--no-forms", dest="forms", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None, help="profiling mode, e.g. transform:9,9,8:h:f64")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
