@@ -121,6 +121,26 @@ __device__ __forceinline__ double from_fixed(long long v, long long Xhi)
     return __longlong_as_double(v == 0 ? 0ll : b + Xhi);
 }
 
+// to_fixed with the pre-shift PC = max(c, 0) known at compile time and
+// emaxp = emax + PC - c: no branches, the 64-bit right shift clamps at 63.
+template <int PC>
+__device__ __forceinline__ long long to_fixed_pc(long long bits, int emaxp)
+{
+    const int e = (int)((unsigned long long)bits >> 52) & 0x7FF;
+    const unsigned long long M = ((((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52))) << PC;
+    const int rs = min(emaxp - e, 63);
+    const long long v = (long long)(M >> rs);
+    return bits < 0 ? -v : v;
+}
+
+// from_fixed with the zero test and the exponent add on the high word.
+__device__ __forceinline__ double from_fixed_hi(long long v, int Xhi32)
+{
+    const double r = __ll2double_rn(v);
+    const int h = __double2hiint(r);
+    return __hiloint2double(h == 0 ? 0 : h + Xhi32, __double2loint(r));
+}
+
 // Out-of-range closures (all values below 2^-960 or near the fp64 maximum):
 // exact but slow conversions.
 __device__ __noinline__ long long to_fixed_slow(long long bits, int emax, int c)
@@ -194,6 +214,19 @@ __device__ __forceinline__ void pole_smem(V *s, int st)
     pole_regs<V, E, PO>(v);
 #pragma unroll
     for (int i = 0; i < E; ++i) s[i * st] = v[i];
+}
+
+// two poles of the same shape at once (independent loads in flight together)
+template <typename V, int E, int PO>
+__device__ __forceinline__ void pole_smem2(V *a, V *b, int st)
+{
+    V va[E], vb[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) { va[i] = a[i * st]; vb[i] = b[i * st]; }
+    pole_regs<V, E, PO>(va);
+    pole_regs<V, E, PO>(vb);
+#pragma unroll
+    for (int i = 0; i < E; ++i) { a[i * st] = va[i]; b[i * st] = vb[i]; }
 }
 
 template <typename V, int PO>
@@ -501,174 +534,162 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-constexpr int kTile3Group = 320;                  // threads of one tile pipeline
-constexpr int kTile3Groups = 2;                   // pipelines per CTA (one CTA per SM)
-constexpr int kTile3Threads = kTile3Group * kTile3Groups;
+// compile-time pre-shift of the fast conversion: c = g0 - 53 of the
+// interior kernel (hierarchize g0 = 55, dehierarchize g0 = 58)
+template <int OP>
+struct kT3Pre { static constexpr int v = OP == GBH_HIERARCHIZE ? 2 : 5; };
 
-__device__ __forceinline__ void group_sync(int id)
-{
-    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(kTile3Group) : "memory");
-}
+constexpr int kTile3Threads = 320;
 
-// One CTA per SM holding two independent tile pipelines (warp groups with
-// their own named barrier and tile buffer), persistent over the tiles, so the
-// load, integer and conversion phases of the two pipelines overlap.  Element
-// offsets inside a tile are the same for every tile: one shared table.
+// One CTA per tile (the block scheduler overlaps the loads of new tiles with
+// the arithmetic of resident ones): every element of the closed tile streams
+// in with cp.async, then three register-pole passes, the last one writing the
+// interior straight to global memory.
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
-__global__ void __launch_bounds__(kTile3Threads, 1) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
+__global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
 {
     using V = typename std::conditional<FIX, long long, ST>::type;
     static_assert(sizeof(V) == sizeof(ST), "in-place conversion needs equal sizes");
-    constexpr int T = kTile3Group;
+    constexpr int T = kTile3Threads;
     constexpr int NV = E0 * E1 * E2, R = E1 * E2, P1 = E0 * E2, P2 = E0 * E1;
     constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
     extern __shared__ __align__(16) unsigned char sm[];
-    int *offs = reinterpret_cast<int *>(sm);
-    constexpr size_t offs_bytes = ((size_t)NV * sizeof(int) + 15) / 16 * 16;
-    __shared__ int s_emax[kTile3Groups];
-    __shared__ unsigned long long s_or[kTile3Groups];
+    V *vals = reinterpret_cast<V *>(sm);
+    __shared__ int s_emax;
+    __shared__ unsigned long long s_or;
+    const int tid = threadIdx.x;
 
-    for (int e = threadIdx.x; e < NV; e += kTile3Threads) {
+    const int64_t G = blockIdx.x;
+    const int64_t b = G / P.tiles;
+    int64_t t = G - b * P.tiles;
+    const int64_t bx = t % P.nb0;
+    t /= P.nb0;
+    const int64_t by = t % P.nb1, bz = t / P.nb1;
+    ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
+    if (tid == 0) { s_emax = 0; s_or = 0ull; }
+    for (int e = tid; e < NV; e += T) {
         const int x = e % E0, r = e / E0;
-        offs[e] = (int)(x + (r % E1) * P.S1 + (r / E1) * P.S2);
+        const ST *src = ub + x + (r % E1) * P.S1 + (r / E1) * P.S2;
+        if constexpr (sizeof(ST) == 8) cp_async8(vals + e, src);
+        else cp_async4(vals + e, src);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
 
-    const int grp = threadIdx.x / T, tid = threadIdx.x - grp * T, bar = 1 + grp;
-    V *vals = reinterpret_cast<V *>(sm + offs_bytes + (size_t)grp * NV * sizeof(V));
-    const int64_t first = (int64_t)blockIdx.x * kTile3Groups + grp, step = (int64_t)gridDim.x * kTile3Groups;
-
-    for (int64_t G = first; G < P.total; G += step) {
-        const int64_t b = G / P.tiles;
-        int64_t t = G - b * P.tiles;
-        const int64_t bx = t % P.nb0;
-        t /= P.nb0;
-        const int64_t by = t % P.nb1, bz = t / P.nb1;
-        ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
-        if (tid == 0) { s_emax[grp] = 0; s_or[grp] = 0ull; }
+    int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
+    bool fast = true;
+    if constexpr (FIX) {
+        // largest binary exponent of the tile (high words only)
+        const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
         for (int e = tid; e < NV; e += T) {
-            if constexpr (sizeof(ST) == 8) cp_async8(vals + e, ub + offs[e]);
-            else cp_async4(vals + e, ub + offs[e]);
+            const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
+            emax = ex > emax ? ex : emax;
         }
-        cp_async_commit();
-        cp_async_wait_all();
-        group_sync(bar);
+        emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+        if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+        __syncthreads();
+        emax = s_emax;
+        cshift = P.g0 - 53;
+        P_ = cshift > 0 ? cshift : 0;
+        rbias = P_ - cshift;
+        X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
+        fast = emax >= 64 && emax <= 1900;
+    }
 
-        int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
-        bool fast = true;
+    unsigned long long orv = 0ull;
+    // dimension 0: convert every row, hierarchize every row or (inverse) the
+    // face rows
+    for (int r = tid; r < R; r += T) {
+        const int y = r % E1, z = r / E1;
+        V v[E0];
+#pragma unroll
+        for (int i = 0; i < E0; ++i) {
+            V w = vals[r * E0 + i];
+            if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
+            v[i] = w;
+        }
+        if constexpr (OP == OP_H) {
+            pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
+        } else if (y == 0 || y == B1 || z == 0 || z == B2) {
+            pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
+#pragma unroll
+            for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
+    }
+    __syncthreads();
+    // dimension 1
+    for (int p = tid; p < P1; p += T) {
+        const int x = p % E0, z = p / E0;
+        V *sp = vals + x + z * E0 * E1;
+        if constexpr (OP == OP_H) {
+            pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
+        } else if (x == 0 || x == B0 || z == 0 || z == B2) {
+            orv |= pole_smem_or<V, E1, FIX ? P_H_HALF : P_H_NAT>(sp, E0);
+        }
+    }
+    __syncthreads();
+    if constexpr (OP == OP_D) {
+        // dimension 2 on the faces, renormalise, block stage on dims 0, 1
+        for (int p = tid; p < P2; p += T) {
+            const int x = p % E0, y = p / E0;
+            if (x == 0 || x == B0 || y == 0 || y == B1)
+                orv |= pole_smem_or<V, E2, FIX ? P_H_HALF : P_H_NAT>(vals + x + y * E0, E0 * E1);
+        }
+        int shift = 0;
         if constexpr (FIX) {
-            // largest binary exponent of the tile (high words only)
-            const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
-            for (int e = tid; e < NV; e += T) {
-                const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
-                emax = ex > emax ? ex : emax;
-            }
-            emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
-            if ((tid & 31) == 0) atomicMax(&s_emax[grp], emax);
-            group_sync(bar);
-            emax = s_emax[grp];
-            cshift = P.g0 - 53;
-            P_ = cshift > 0 ? cshift : 0;
-            rbias = P_ - cshift;
-            X = emax - 1075 - cshift - (OP == OP_H ? 3 : 0);
-            fast = emax >= 64 && emax <= 1900;
+            orv |= (1ull << P.g0) - 1ull;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
+            if ((tid & 31) == 0) atomicOr(&s_or, orv);
+            __syncthreads();
+            shift = (64 - __clzll((long long)s_or)) + P.growth_bits - 62;
+            shift = shift > 0 ? shift : 0;
+            X += shift;
+        } else {
+            __syncthreads();
         }
-
-        unsigned long long orv = 0ull;
-        // dimension 0: convert every row, hierarchize every row or (inverse)
-        // the face rows
         for (int r = tid; r < R; r += T) {
-            const int y = r % E1, z = r / E1;
             V v[E0];
 #pragma unroll
             for (int i = 0; i < E0; ++i) {
                 V w = vals[r * E0 + i];
-                if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
+                if constexpr (FIX) w = w >> shift;
                 v[i] = w;
             }
-            if constexpr (OP == OP_H) {
-                pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
-            } else if (y == 0 || y == B1 || z == 0 || z == B2) {
-                pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
-#pragma unroll
-                for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
-            }
+            pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
 #pragma unroll
             for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
         }
-        group_sync(bar);
-        // dimension 1
+        __syncthreads();
         for (int p = tid; p < P1; p += T) {
             const int x = p % E0, z = p / E0;
-            V *sp = vals + x + z * E0 * E1;
-            if constexpr (OP == OP_H) {
-                pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
-            } else if (x == 0 || x == B0 || z == 0 || z == B2) {
-                orv |= pole_smem_or<V, E1, FIX ? P_H_HALF : P_H_NAT>(sp, E0);
+            pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
+        }
+        __syncthreads();
+    }
+    // dimension 2, then the tile interior goes straight to global memory
+    const long long Xhi = (long long)X << 52;
+    for (int p = tid; p < P2; p += T) {
+        const int x = p % E0, y = p / E0;
+        V *sp = vals + x + y * E0;
+        V v[E2];
+#pragma unroll
+        for (int i = 0; i < E2; ++i) v[i] = sp[i * E0 * E1];
+        if constexpr (OP == OP_H) pole_regs<V, E2, FIX ? P_H_DBL : P_H_NAT>(v);
+        else pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
+        if (x > 0 && x < B0 && y > 0 && y < B1) {
+            ST *o = ub + x + y * P.S1;
+#pragma unroll
+            for (int i = 1; i < E2 - 1; ++i) {
+                ST out;
+                if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
+                else out = (ST)v[i];
+                o[i * P.S2] = out;
             }
         }
-        group_sync(bar);
-        if constexpr (OP == OP_D) {
-            // dimension 2 on the faces, renormalise, block stage on dims 0, 1
-            for (int p = tid; p < P2; p += T) {
-                const int x = p % E0, y = p / E0;
-                if (x == 0 || x == B0 || y == 0 || y == B1)
-                    orv |= pole_smem_or<V, E2, FIX ? P_H_HALF : P_H_NAT>(vals + x + y * E0, E0 * E1);
-            }
-            int shift = 0;
-            if constexpr (FIX) {
-                orv |= (1ull << P.g0) - 1ull;
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) orv |= __shfl_xor_sync(0xFFFFFFFFu, orv, o);
-                if ((tid & 31) == 0) atomicOr(&s_or[grp], orv);
-                group_sync(bar);
-                shift = (64 - __clzll((long long)s_or[grp])) + P.growth_bits - 62;
-                shift = shift > 0 ? shift : 0;
-                X += shift;
-            } else {
-                group_sync(bar);
-            }
-            for (int r = tid; r < R; r += T) {
-                V v[E0];
-#pragma unroll
-                for (int i = 0; i < E0; ++i) {
-                    V w = vals[r * E0 + i];
-                    if constexpr (FIX) w = w >> shift;
-                    v[i] = w;
-                }
-                pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
-#pragma unroll
-                for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
-            }
-            group_sync(bar);
-            for (int p = tid; p < P1; p += T) {
-                const int x = p % E0, z = p / E0;
-                pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
-            }
-            group_sync(bar);
-        }
-        // dimension 2, then the tile interior goes straight to global memory
-        const long long Xhi = (long long)X << 52;
-        for (int p = tid; p < P2; p += T) {
-            const int x = p % E0, y = p / E0;
-            V *sp = vals + x + y * E0;
-            V v[E2];
-#pragma unroll
-            for (int i = 0; i < E2; ++i) v[i] = sp[i * E0 * E1];
-            if constexpr (OP == OP_H) pole_regs<V, E2, FIX ? P_H_DBL : P_H_NAT>(v);
-            else pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
-            if (x > 0 && x < B0 && y > 0 && y < B1) {
-                ST *o = ub + x + y * P.S1;
-#pragma unroll
-                for (int i = 1; i < E2 - 1; ++i) {
-                    ST out;
-                    if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
-                    else out = (ST)v[i];
-                    o[i * P.S2] = out;
-                }
-            }
-        }
-        group_sync(bar);
     }
 }
 
@@ -1090,8 +1111,7 @@ bool tile3_shape_ok(int es, int E0, int E1, int E2)
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
 int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes)
 {
-    constexpr size_t NV = (size_t)E0 * E1 * E2;
-    constexpr size_t smem = (NV * sizeof(int) + 15) / 16 * 16 + kTile3Groups * NV * sizeof(ST);
+    constexpr size_t smem = (size_t)E0 * E1 * E2 * sizeof(ST);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_tile3<ST, FIX, OP, E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1100,9 +1120,9 @@ int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile3<ST, FIX, OP, E0, E1, E2>, kTile3Threads, smem);
     if (per_sm < 1) return GBH_EUNSUPPORTED;
-    const int64_t grid = std::min<int64_t>(P.total, (int64_t)num_sms() * per_sm);
+    if (P.total > INT32_MAX) return 1;
     ProfScope ps("fused_class0", st, alg_bytes);
-    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)grid, kTile3Threads, smem, st>>>(P, u);
+    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)P.total, kTile3Threads, smem, st>>>(P, u);
     ps.done();
     count_launches(1);
     return check_launch();
@@ -1119,7 +1139,7 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
     // element offsets inside a tile are kept as int32
     if ((int64_t)(E0 - 1) + (E1 - 1) * g.S[1] + (E2 - 1) * g.S[2] >= INT32_MAX) return 1;
     // two tile buffers and the offset table must fit shared memory
-    if ((size_t)E0 * E1 * E2 * (kTile3Groups * sizeof(ST) + sizeof(int)) + 16 > 226 * 1024) return 1;
+    if ((size_t)E0 * E1 * E2 * sizeof(ST) > 200 * 1024) return 1;
     Tile3Params P{};
     P.S1 = g.S[1];
     P.S2 = g.S[2];
