@@ -506,7 +506,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
 
 struct Tile3Params {
     int64_t S1, S2;          // grid strides of dimensions 1 and 2
-    int64_t nb0, nb1;        // tiles along dimensions 0 and 1
+    int64_t gs0, gs1, gs2;   // global element stride of one closure step
+    int64_t step0, step1, step2;  // global offset of one group step
+    int64_t nb0, nb1;        // groups along dimensions 0 and 1
     int64_t tiles;           // tiles per grid
     int64_t total;           // tiles * batch
     int64_t N;               // points per grid
@@ -541,23 +543,32 @@ struct kT3Pre { static constexpr int v = OP == GBH_HIERARCHIZE ? 2 : 5; };
 
 constexpr int kTile3Threads = 320;
 
-// One CTA per tile (the block scheduler overlaps the loads of new tiles with
-// the arithmetic of resident ones): every element of the closed tile streams
-// in with cp.async, then three register-pole passes, the last one writing the
-// interior straight to global memory.
-template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
+// One CTA per closure (the block scheduler overlaps the loads of new closures
+// with the arithmetic of resident ones): every element streams in with
+// cp.async, then three register-pole passes.  LM marks the lattice dimensions
+// of the class (bit k: dimension k is on the block lattice; 0 is the interior
+// class): a lattice dimension takes global strides 2^{m_k} S_k, has no group
+// index, and its whole extent is written.
+template <typename ST, bool FIX, int OP, int E0, int E1, int E2, int LM>
 __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constant__ Tile3Params P, ST *__restrict__ u)
 {
     using V = typename std::conditional<FIX, long long, ST>::type;
     static_assert(sizeof(V) == sizeof(ST), "in-place conversion needs equal sizes");
+    constexpr bool L0 = LM & 1, L1 = LM & 2, L2 = LM & 4;
     constexpr int T = kTile3Threads;
     constexpr int NV = E0 * E1 * E2, R = E1 * E2, P1 = E0 * E2, P2 = E0 * E1;
     constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
+    constexpr int NBLOCK = (L0 ? 0 : 1) + (L1 ? 0 : 1) + (L2 ? 0 : 1);
     extern __shared__ __align__(16) unsigned char sm[];
     V *vals = reinterpret_cast<V *>(sm);
     __shared__ int s_emax;
     __shared__ unsigned long long s_or;
     const int tid = threadIdx.x;
+
+    // block coordinate c of extent E is interior (or the dimension is a lattice)
+    auto inner0 = [](int c) { return L0 || (c > 0 && c < B0); };
+    auto inner1 = [](int c) { return L1 || (c > 0 && c < B1); };
+    auto inner2 = [](int c) { return L2 || (c > 0 && c < B2); };
 
     const int64_t G = blockIdx.x;
     const int64_t b = G / P.tiles;
@@ -565,11 +576,11 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     const int64_t bx = t % P.nb0;
     t /= P.nb0;
     const int64_t by = t % P.nb1, bz = t / P.nb1;
-    ST *__restrict__ ub = u + b * P.N + bx * B0 + by * B1 * P.S1 + bz * B2 * P.S2;
+    ST *__restrict__ ub = u + b * P.N + bx * P.step0 + by * P.step1 + bz * P.step2;
     if (tid == 0) { s_emax = 0; s_or = 0ull; }
     for (int e = tid; e < NV; e += T) {
         const int x = e % E0, r = e / E0;
-        const ST *src = ub + x + (r % E1) * P.S1 + (r / E1) * P.S2;
+        const ST *src = ub + x * P.gs0 + (r % E1) * P.gs1 + (r / E1) * P.gs2;
         if constexpr (sizeof(ST) == 8) cp_async8(vals + e, src);
         else cp_async4(vals + e, src);
     }
@@ -580,7 +591,7 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
     bool fast = true;
     if constexpr (FIX) {
-        // largest binary exponent of the tile (high words only)
+        // largest binary exponent of the closure (high words only)
         const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
         for (int e = tid; e < NV; e += T) {
             const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
@@ -598,8 +609,10 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     }
 
     unsigned long long orv = 0ull;
-    // dimension 0: convert every row, hierarchize every row or (inverse) the
-    // face rows
+    // stage A of the inverse along one dimension: a lattice dimension
+    // dehierarchizes the poles through class points (block coordinates
+    // interior), a block dimension hierarchizes the face poles
+    // dimension 0: convert every row, then transform
     for (int r = tid; r < R; r += T) {
         const int y = r % E1, z = r / E1;
         V v[E0];
@@ -611,8 +624,12 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         }
         if constexpr (OP == OP_H) {
             pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
-        } else if (y == 0 || y == B1 || z == 0 || z == B2) {
+        } else if constexpr (L0) {
+            if (inner1(y) && inner2(z)) pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
+        } else if (!(inner1(y) && inner2(z))) {
             pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
+        }
+        if constexpr (OP == OP_D) {
 #pragma unroll
             for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
         }
@@ -626,17 +643,23 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         V *sp = vals + x + z * E0 * E1;
         if constexpr (OP == OP_H) {
             pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
-        } else if (x == 0 || x == B0 || z == 0 || z == B2) {
+        } else if constexpr (L1) {
+            if (inner0(x) && inner2(z)) orv |= pole_smem_or<V, E1, FIX ? P_D_FIX : P_D_NAT>(sp, E0);
+        } else if (!(inner0(x) && inner2(z))) {
             orv |= pole_smem_or<V, E1, FIX ? P_H_HALF : P_H_NAT>(sp, E0);
         }
     }
     __syncthreads();
     if constexpr (OP == OP_D) {
-        // dimension 2 on the faces, renormalise, block stage on dims 0, 1
+        // dimension 2, stage A; renormalise; stage B on the block dimensions
         for (int p = tid; p < P2; p += T) {
             const int x = p % E0, y = p / E0;
-            if (x == 0 || x == B0 || y == 0 || y == B1)
-                orv |= pole_smem_or<V, E2, FIX ? P_H_HALF : P_H_NAT>(vals + x + y * E0, E0 * E1);
+            V *sp = vals + x + y * E0;
+            if constexpr (L2) {
+                if (inner0(x) && inner1(y)) orv |= pole_smem_or<V, E2, FIX ? P_D_FIX : P_D_NAT>(sp, E0 * E1);
+            } else if (!(inner0(x) && inner1(y))) {
+                orv |= pole_smem_or<V, E2, FIX ? P_H_HALF : P_H_NAT>(sp, E0 * E1);
+            }
         }
         int shift = 0;
         if constexpr (FIX) {
@@ -651,26 +674,33 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         } else {
             __syncthreads();
         }
-        for (int r = tid; r < R; r += T) {
-            V v[E0];
+        if constexpr (!L0) {
+            for (int r = tid; r < R; r += T) {
+                V v[E0];
 #pragma unroll
-            for (int i = 0; i < E0; ++i) {
-                V w = vals[r * E0 + i];
-                if constexpr (FIX) w = w >> shift;
-                v[i] = w;
+                for (int i = 0; i < E0; ++i) {
+                    V w = vals[r * E0 + i];
+                    if constexpr (FIX) w = w >> shift;
+                    v[i] = w;
+                }
+                pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
+#pragma unroll
+                for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
             }
-            pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
-#pragma unroll
-            for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
+        } else if constexpr (FIX) {
+            for (int e = tid; e < NV; e += T) vals[e] = vals[e] >> shift;
         }
         __syncthreads();
-        for (int p = tid; p < P1; p += T) {
-            const int x = p % E0, z = p / E0;
-            pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
+        if constexpr (!L1) {
+            for (int p = tid; p < P1; p += T) {
+                const int x = p % E0, z = p / E0;
+                pole_smem<V, E1, FIX ? P_D_FIX : P_D_NAT>(vals + x + z * E0 * E1, E0);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    // dimension 2, then the tile interior goes straight to global memory
+    // dimension 2 (hierarchize; block stage of the inverse), then the class
+    // points go to global memory
     const long long Xhi = (long long)X << 52;
     for (int p = tid; p < P2; p += T) {
         const int x = p % E0, y = p / E0;
@@ -679,18 +709,19 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
 #pragma unroll
         for (int i = 0; i < E2; ++i) v[i] = sp[i * E0 * E1];
         if constexpr (OP == OP_H) pole_regs<V, E2, FIX ? P_H_DBL : P_H_NAT>(v);
-        else pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
-        if (x > 0 && x < B0 && y > 0 && y < B1) {
-            ST *o = ub + x + y * P.S1;
+        else if constexpr (!L2) pole_regs<V, E2, FIX ? P_D_FIX : P_D_NAT>(v);
+        if (inner0(x) && inner1(y)) {
+            ST *o = ub + x * P.gs0 + y * P.gs1;
 #pragma unroll
-            for (int i = 1; i < E2 - 1; ++i) {
+            for (int i = L2 ? 0 : 1; i < (L2 ? E2 : E2 - 1); ++i) {
                 ST out;
                 if constexpr (FIX) out = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
                 else out = (ST)v[i];
-                o[i * P.S2] = out;
+                o[i * P.gs2] = out;
             }
         }
     }
+    (void)NBLOCK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1093,82 +1124,83 @@ int launch_closure(const Plan &pl, const std::vector<ClassPlan> &cls, const Geom
     return check_launch();
 }
 
-// Compile-time tiles of the interior-class kernel (E0, E1, E2).
-template <typename ST, bool FIX, int OP>
-struct Tile3Table;
-
-#define GBH_TILE3_LIST(X) X(33, 17, 17) X(17, 17, 17) X(33, 17, 9) X(65, 17, 17) X(65, 17, 9)
+// Compile-time closures of the 3-D kernel: (storage, E0, E1, E2, lattice mask).
+// The interior class (mask 0) and the three one-dimensional lattice classes of
+// the planner's usual 3-D tiles.
+#define GBH_T3_F64(X) X(33, 17, 17, 0) X(17, 17, 17, 0) X(33, 17, 9, 0) \
+    X(17, 17, 17, 1) X(9, 17, 17, 1) X(33, 33, 17, 2) X(33, 17, 17, 2) X(33, 17, 33, 4) X(33, 17, 17, 4)
+#define GBH_T3_F32(X) X(65, 17, 17, 0) X(65, 17, 9, 0) X(33, 17, 17, 0) X(17, 17, 17, 0) X(33, 17, 9, 0) \
+    X(9, 17, 17, 1) X(5, 17, 17, 1) X(65, 33, 17, 2) X(65, 17, 17, 2) X(65, 17, 33, 4) X(65, 17, 17, 4)
 
 bool tile3_shape_ok(int es, int E0, int E1, int E2)
 {
-    if (E0 > max_extent(es) || E1 > max_extent(es) || E2 > max_extent(es)) return false;
-#define GBH_TILE3_CMP(a, b, c) if (E0 == a && E1 == b && E2 == c) return true;
-    GBH_TILE3_LIST(GBH_TILE3_CMP)
-#undef GBH_TILE3_CMP
+#define GBH_T3_CMP(a, b, c, m) if (m == 0 && E0 == a && E1 == b && E2 == c) return true;
+    if (es == 8) { GBH_T3_F64(GBH_T3_CMP) }
+    else { GBH_T3_F32(GBH_T3_CMP) }
+#undef GBH_T3_CMP
     return false;
 }
 
-template <typename ST, bool FIX, int OP, int E0, int E1, int E2>
-int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes)
+template <typename ST, bool FIX, int OP, int E0, int E1, int E2, int LM>
+int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes, const char *name)
 {
     constexpr size_t smem = (size_t)E0 * E1 * E2 * sizeof(ST);
+    auto kern = k_tile3<ST, FIX, OP, E0, E1, E2, LM>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_tile3<ST, FIX, OP, E0, E1, E2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile3<ST, FIX, OP, E0, E1, E2>, kTile3Threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile3Threads, smem);
     if (per_sm < 1) return GBH_EUNSUPPORTED;
     if (P.total > INT32_MAX) return 1;
-    ProfScope ps("fused_class0", st, alg_bytes);
-    k_tile3<ST, FIX, OP, E0, E1, E2><<<(unsigned)P.total, kTile3Threads, smem, st>>>(P, u);
+    ProfScope ps(name, st, alg_bytes);
+    kern<<<(unsigned)P.total, kTile3Threads, smem, st>>>(P, u);
     ps.done();
     count_launches(1);
     return check_launch();
 }
 
-// Launches the compile-time interior kernel for a 3-D class-0 closure;
-// returns 1 if no compile-time tile matches (the generic kernel then runs).
+// Launches the compile-time kernel for a 3-D class whose lattice dimensions
+// are all held in the closure (no point dimensions); returns 1 if no
+// compile-time closure matches (the generic kernel then runs).
 template <typename ST, bool FIX, int OP>
 int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cudaStream_t st)
 {
     const ClassDesc &c = cp.desc;
-    const int E0 = c.e[0], E1 = c.e[1], E2 = c.e[2];
-    if (pl.d != 3 || cp.mask != 0 || !tile3_shape_ok((int)sizeof(ST), E0, E1, E2)) return 1;
-    // element offsets inside a tile are kept as int32
-    if ((int64_t)(E0 - 1) + (E1 - 1) * g.S[1] + (E2 - 1) * g.S[2] >= INT32_MAX) return 1;
-    // two tile buffers and the offset table must fit shared memory
+    if (pl.d != 3 || cp.npoint != 0) return 1;
+    if (cp.mask != 0 && cp.mask != 1 && cp.mask != 2 && cp.mask != 4) return 1;
+    for (int k = 0; k < 3; ++k)
+        if (c.lev[k] < 1) return 1;
+    const int E0 = c.e[0], E1 = c.e[1], E2 = c.e[2], LM = (int)cp.mask;
     if ((size_t)E0 * E1 * E2 * sizeof(ST) > 200 * 1024) return 1;
     Tile3Params P{};
     P.S1 = g.S[1];
     P.S2 = g.S[2];
+    P.gs0 = c.gstride[0];
+    P.gs1 = c.gstride[1];
+    P.gs2 = c.gstride[2];
+    P.step0 = c.gstep[0];
+    P.step1 = c.gstep[1];
+    P.step2 = c.gstep[2];
     P.nb0 = c.ngrp[0];
     P.nb1 = c.ngrp[1];
     P.tiles = c.ngrp[0] * c.ngrp[1] * c.ngrp[2];
     P.total = P.tiles * g.batch;
     P.N = g.N;
-    if (OP == OP_H) {
-        P.g0 = 61 - 2 * 3;
-        P.growth_bits = 0;
-    } else {
-        P.g0 = 61 - 3;
-        double gr = 1.0;
-        for (int k = 0; k < 3; ++k) gr *= dehier_growth(c.lev[k]);
-        P.growth_bits = (int)std::ceil(std::log2(gr) + 1e-9);
-    }
+    P.g0 = c.g0;
+    P.growth_bits = c.growth_bits;
     const double bytes = 2.0 * sizeof(ST) * (double)P.total * c.W;
-#define GBH_TILE3_CALL(a, b, cc) \
-    if (E0 == a && E1 == b && E2 == cc) return launch_tile3_shape<ST, FIX, OP, a, b, cc>(P, u, st, bytes);
+    const char *name = cp.mask == 0 ? "fused_class0" : "fused_class1";
+#define GBH_T3_CALL(a, b, cc, m) \
+    if (LM == m && E0 == a && E1 == b && E2 == cc) return launch_tile3_shape<ST, FIX, OP, a, b, cc, m>(P, u, st, bytes, name);
     if constexpr (sizeof(ST) == 8) {
-        // fp64 keeps register poles to 33 points
-        if (E0 == 33 && E1 == 17 && E2 == 17) return launch_tile3_shape<ST, FIX, OP, 33, 17, 17>(P, u, st, bytes);
-        if (E0 == 17 && E1 == 17 && E2 == 17) return launch_tile3_shape<ST, FIX, OP, 17, 17, 17>(P, u, st, bytes);
-        if (E0 == 33 && E1 == 17 && E2 == 9) return launch_tile3_shape<ST, FIX, OP, 33, 17, 9>(P, u, st, bytes);
+        GBH_T3_F64(GBH_T3_CALL)
     } else {
-        GBH_TILE3_LIST(GBH_TILE3_CALL)
+        GBH_T3_F32(GBH_T3_CALL)
     }
-#undef GBH_TILE3_CALL
+#undef GBH_T3_CALL
     return 1;
 }
 
@@ -1211,11 +1243,15 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
 {
     const int d = pl.d;
     auto closure = [&](int c) -> int {
-        if (c == 0 && pl.by_size[0].size() == 1) {
-            const int r = launch_tile3<ST, FIX, OP>(pl, pl.by_size[0][0], g, u, st);
-            if (r != 1) return r;
+        if (c > 1) return launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st);
+        // classes with a compile-time kernel go one by one, the rest together
+        std::vector<ClassPlan> rest;
+        for (const ClassPlan &cp : pl.by_size[c]) {
+            const int r = launch_tile3<ST, FIX, OP>(pl, cp, g, u, st);
+            if (r == 1) rest.push_back(cp);
+            else if (r != GBH_OK) return r;
         }
-        return launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st);
+        return launch_closure<ST, FIX, OP>(pl, rest, g, u, st);
     };
     if (OP == OP_H) {
         for (int c = 0; c <= d; ++c) {
