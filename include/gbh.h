@@ -95,7 +95,8 @@ int gbh_hierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype,
 /* Execution path of gbh_transform. */
 typedef enum {
     GBH_PATH_AUTO = 0,   /* planner's choice (fused when available)             */
-    GBH_PATH_PLAIN = 1,  /* one sweep kernel per dimension, native arithmetic   */
+    GBH_PATH_PLAIN = 1,  /* one sweep kernel per dimension (native arithmetic
+                            unless arith = 2)                                   */
     GBH_PATH_FUSED = 2   /* dyadic-tile kernels, all dimensions per tile        */
 } gbh_path;
 
@@ -105,8 +106,10 @@ typedef struct {
     int32_t tile_exp[16];  /* fused path: tile exponent m_k per dimension
                               (tile edge 2^{m_k}+1, 0 <= m_k <= l_k); all 0 =
                               the planner chooses                               */
-    int32_t arith;         /* fused path, GBH_F64: 0 = planner's choice,
-                              1 = native fp64, 2 = int64 block fixed point       */
+    int32_t arith;         /* GBH_F64 only: 0 = the path's default (native fp64
+                              on GBH_PATH_PLAIN, int64 block fixed point on the
+                              others), 1 = native fp64, 2 = int64 block fixed
+                              point (one binary scale per tile or pole group)    */
     int32_t reserved[6];
 } gbh_options;
 

@@ -165,7 +165,7 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     const int path = opt ? opt->path : GBH_PATH_AUTO;
     if (path != GBH_PATH_AUTO && path != GBH_PATH_PLAIN && path != GBH_PATH_FUSED) return GBH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (path == GBH_PATH_PLAIN) return plain_transform(data, g, dtype, op, s);
+    if (path == GBH_PATH_PLAIN) return plain_transform(data, g, dtype, op, s, opt && opt->arith == 2);
     if (path == GBH_PATH_FUSED) {
         if (!fused_supported(g, dtype, op)) return GBH_EUNSUPPORTED;
         return fused_transform(data, g, dtype, op, opt, s);
@@ -173,7 +173,8 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     // planner's choice: the fused path when it takes the shape and the grid is
     // large enough to tile, else one sweep per dimension
     if (g.N >= 4096 && fused_preferred(g, dtype, op)) return fused_transform(data, g, dtype, op, opt, s);
-    return plain_transform(data, g, dtype, op, s);
+    // fp64 sweeps compute in fixed point unless native arithmetic is asked for
+    return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1));
 }
 
 int gbh_hierarchize(void *data, int d, const int32_t *levels, int dtype, void *stream)

@@ -47,8 +47,10 @@ int check_launch();
 // Number of SMs of the current device (cached per device).
 int num_sms();
 
-// Plain path: one sweep per dimension with native arithmetic.
-int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s);
+// Plain path: one sweep per dimension.  fixed64: fp64 pole groups compute in
+// int64 fixed point (otherwise native arithmetic in the serial operation
+// order, bit-identical to the serial algorithm).
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64 = false);
 
 // Fused path: dyadic tiles (class-ordered), see fused.cu.
 int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,

@@ -14,6 +14,8 @@
 //   level kernel      any dimension with few, long poles: one launch per level,
 //                     threads over (pole, point of that level).
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 
 #include "gbh_internal.h"
 
@@ -221,6 +223,171 @@ __global__ void __launch_bounds__(256) k_level(T *__restrict__ u, int64_t S, int
 }
 
 // ---------------------------------------------------------------------------
+// pole-group kernel: a group of neighbouring poles staged in shared memory
+// ---------------------------------------------------------------------------
+//
+// G poles of one dimension (length n = 2^l + 1, stride S) per CTA, loaded with
+// neighbouring poles side by side (coalesced), swept level by level in shared
+// memory, written back.  Rows of dimension 0 (S = 1) load row after row.
+// FIX (fp64 only): the group is scaled by its largest binary exponent and
+// swept in int64 fixed point (hierarchize exact in the doubling form; the
+// inverse and the transpose add halved sums); one int64 -> fp64 conversion per
+// point instead of two fp64 operations per point.
+constexpr int kGroupElems = 8192;
+
+__device__ __forceinline__ long long g_to_fixed(long long bits, int emax, int c)
+{
+    const int e = (int)((unsigned long long)bits >> 52) & 0x7FF;
+    if (e == 0) return 0;
+    const unsigned long long M = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = c - (emax - e);
+    long long v;
+    if (sh >= 0) v = (long long)(M << sh);
+    else v = (-sh >= 63) ? 0 : (long long)(M >> (-sh));
+    return bits < 0 ? -v : v;
+}
+
+__device__ __forceinline__ double g_from_fixed(long long v, int X)
+{
+    if (v == 0) return 0.0;
+    return ldexp(__ll2double_rn(v), X);
+}
+
+__device__ __forceinline__ double g_from_fixed_fast(long long v, long long Xhi)
+{
+    const long long b = __double_as_longlong(__ll2double_rn(v));
+    return __longlong_as_double(v == 0 ? 0ll : b + Xhi);
+}
+
+template <typename T, int OP, bool FIX, bool ROWS>
+__global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S, int64_t poles, int l, int G,
+                                                    int g0)
+{
+    using V = typename std::conditional<FIX, long long, T>::type;
+    extern __shared__ __align__(16) unsigned char smr[];
+    V *sv = reinterpret_cast<V *>(smr);
+    int64_t *pb = reinterpret_cast<int64_t *>(smr + (size_t)kGroupElems * sizeof(V));
+    __shared__ int s_emax;
+    const int n = (1 << l) + 1, last = 1 << l;
+    const int64_t t0 = (int64_t)blockIdx.x * G;
+    const int Gc = (poles - t0) < (int64_t)G ? (int)(poles - t0) : G;
+    const int cnt = Gc * n;
+    const unsigned magG = Gc == 1 ? 0u : (0xFFFFFFFFu / (unsigned)Gc) + 1u;
+    if (!ROWS)
+        for (int g = threadIdx.x; g < Gc; g += blockDim.x) {
+            const int64_t t = t0 + g, o = t / S;
+            pb[g] = o * S * n + (t - o * S);
+        }
+    if (threadIdx.x == 0) s_emax = 0;
+    __syncthreads();
+    // element w of the group: rows go row after row, poles side by side
+    auto gaddr = [&](int w, int &sidx) -> int64_t {
+        if (ROWS) {
+            sidx = w;
+            return t0 * n + w;
+        }
+        const int i = magG ? (int)__umulhi((unsigned)w, magG) : w, g = w - i * Gc;
+        sidx = g * n + i;
+        return pb[g] + (int64_t)i * S;
+    };
+    int emax = 0;
+    for (int w0 = threadIdx.x; w0 < cnt; w0 += blockDim.x * 4) {
+        T tmp[4];
+        int sid[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = w0 + q * blockDim.x;
+            if (w < cnt) tmp[q] = u[gaddr(w, sid[q])];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int w = w0 + q * blockDim.x;
+            if (w < cnt) {
+                if constexpr (FIX) {
+                    const long long bits = __double_as_longlong((double)tmp[q]);
+                    emax = max(emax, (int)((unsigned long long)bits >> 52) & 0x7FF);
+                    sv[sid[q]] = (V)bits;
+                } else {
+                    sv[sid[q]] = (V)tmp[q];
+                }
+            }
+        }
+    }
+    int X = 0;
+    long long Xhi = 0;
+    bool fast = true;
+    if constexpr (FIX) {
+        emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+        if ((threadIdx.x & 31) == 0) atomicMax(&s_emax, emax);
+        __syncthreads();
+        emax = s_emax;
+        const int c = g0 - 53;
+        X = emax - 1075 - c - (OP == OP_H ? 1 : 0);
+        Xhi = (long long)X << 52;
+        fast = emax >= 64 && emax <= 1900;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) sv[e] = g_to_fixed((long long)sv[e], emax, c);
+    }
+    __syncthreads();
+    // level-ordered sweeps, all poles of the group at once
+    if (OP == OP_H) {
+        for (int lev = l; lev >= 1; --lev) {
+            const int s = 1 << (l - lev), per = 1 << (lev - 1);
+            for (int q = threadIdx.x; q < Gc * per; q += blockDim.x) {
+                const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                V *row = sv + r * n;
+                if constexpr (FIX) row[i] = (row[i] + row[i]) - row[i - s] - row[i + s];
+                else row[i] = row[i] - V(0.5) * (row[i - s] + row[i + s]);
+            }
+            __syncthreads();
+        }
+        if constexpr (FIX) {
+            for (int r = threadIdx.x; r < Gc; r += blockDim.x) {
+                sv[r * n] += sv[r * n];
+                sv[r * n + last] += sv[r * n + last];
+            }
+            __syncthreads();
+        }
+    } else if (OP == OP_D) {
+        for (int lev = 1; lev <= l; ++lev) {
+            const int s = 1 << (l - lev), per = 1 << (lev - 1);
+            for (int q = threadIdx.x; q < Gc * per; q += blockDim.x) {
+                const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
+                V *row = sv + r * n;
+                if constexpr (FIX) row[i] = row[i] + ((row[i - s] + row[i + s]) >> 1);
+                else row[i] = row[i] + V(0.5) * (row[i - s] + row[i + s]);
+            }
+            __syncthreads();
+        }
+    } else {
+        // transpose: level by level coarse to fine, every parent p = 2 s q
+        // collects its two children of this level (left, then right)
+        for (int lev = 1; lev <= l; ++lev) {
+            const int s = 1 << (l - lev), per = (1 << (lev - 1)) + 1;
+            for (int w = threadIdx.x; w < Gc * per; w += blockDim.x) {
+                const int r = w / per, q = w - r * per, p = 2 * s * q;
+                V *row = sv + r * n;
+                if constexpr (FIX) {
+                    const V lc = q > 0 ? row[p - s] : V(0), rc = q < per - 1 ? row[p + s] : V(0);
+                    row[p] = row[p] - ((lc + rc) >> 1);
+                } else {
+                    V y = row[p];
+                    if (q > 0) y = y - V(0.5) * row[p - s];
+                    if (q < per - 1) y = y - V(0.5) * row[p + s];
+                    row[p] = y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+        int sidx;
+        const int64_t a = gaddr(w, sidx);
+        if constexpr (FIX) u[a] = fast ? (T)g_from_fixed_fast((long long)sv[sidx], Xhi) : (T)g_from_fixed((long long)sv[sidx], X);
+        else u[a] = (T)sv[sidx];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
 
@@ -269,11 +436,44 @@ int sweep_level(T *u, const Geom &g, int k, cudaStream_t st)
     return GBH_OK;
 }
 
+template <typename T, int OP, bool FIX, bool ROWS>
+int launch_group(T *u, const Geom &g, int k, cudaStream_t st)
+{
+    const int l = g.l[k];
+    const int n = (int)g.n[k];
+    const int64_t poles = g.total / g.n[k];
+    const int G = std::max(1, kGroupElems / n);
+    const int64_t blocks = (poles + G - 1) / G;
+    if (blocks > INT32_MAX) return GBH_ERANGE;
+    using V = typename std::conditional<FIX, long long, T>::type;
+    const size_t smem = (size_t)kGroupElems * sizeof(V) + (size_t)G * sizeof(int64_t) + 16;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_pole_group<T, OP, FIX, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kGroupElems * sizeof(long long) + kGroupElems * sizeof(int64_t) + 16));
+        attr = true;
+    }
+    // fixed point headroom: hierarchize doubles once; the inverse grows by at
+    // most l + 1 (sum of hat weights); the transpose by at most l + 1
+    const int g0 = OP == OP_H ? 59 : 59 - (int)std::ceil(std::log2((double)l + 1.0));
+    ProfScope ps(ROWS ? "plain_rows_group" : "plain_pole_group", st, 2.0 * sizeof(T) * (double)g.total);
+    k_pole_group<T, OP, FIX, ROWS><<<(unsigned)blocks, 256, smem, st>>>(u, g.S[k], poles, l, G, g0);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
 template <typename T, int OP>
-int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st)
+int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
 {
     const int l = g.l[k];
     const int64_t poles = g.total / g.n[k];
+    if constexpr (sizeof(T) == 8) {
+        if (fixed && g.n[k] <= kGroupElems) {
+            if (k == 0) return launch_group<T, OP, true, true>(u, g, k, st);
+            return launch_group<T, OP, true, false>(u, g, k, st);
+        }
+    }
     if (k == 0) {
         if (g.n[0] > kRowCapElems) return sweep_level<T, OP>(u, g, 0, st);
         const int n = (int)g.n[0];
@@ -302,6 +502,7 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st)
             default: return launch_pole_regs<T, OP, 5>(u, g.S[k], poles, st);
         }
     }
+    if (g.n[k] <= kGroupElems) return launch_group<T, OP, false, false>(u, g, k, st);
     if (poles < kMinPolesForThreadPerPole) return sweep_level<T, OP>(u, g, k, st);
     ProfScope ps("plain_pole_global", st, 2.0 * sizeof(T) * (double)g.total);
     k_pole_global<T, OP><<<grid_for(poles, 256), 256, 0, st>>>(u, g.S[k], poles, l);
@@ -311,32 +512,32 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st)
 }
 
 template <typename T, int OP>
-int plain_all(T *u, const Geom &g, cudaStream_t st)
+int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed)
 {
     for (int k = 0; k < g.d; ++k) {
         if (g.l[k] == 0) continue;
-        if (int e = sweep_dim<T, OP>(u, g, k, st)) return e;
+        if (int e = sweep_dim<T, OP>(u, g, k, st, fixed)) return e;
     }
     return GBH_OK;
 }
 
 template <typename T>
-int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st)
+int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed)
 {
     switch (op) {
-        case OP_H: return plain_all<T, OP_H>(u, g, st);
-        case OP_D: return plain_all<T, OP_D>(u, g, st);
-        case OP_A: return plain_all<T, OP_A>(u, g, st);
+        case OP_H: return plain_all<T, OP_H>(u, g, st, fixed);
+        case OP_D: return plain_all<T, OP_D>(u, g, st, fixed);
+        case OP_A: return plain_all<T, OP_A>(u, g, st, fixed);
         default: return GBH_EINVAL;
     }
 }
 
 }  // namespace
 
-int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s)
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64)
 {
-    if (dtype == GBH_F64) return plain_dispatch<double>(static_cast<double *>(data), g, op, s);
-    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s);
+    if (dtype == GBH_F64) return plain_dispatch<double>(static_cast<double *>(data), g, op, s, fixed64);
+    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s, false);
     return GBH_EDTYPE;
 }
 

@@ -90,6 +90,28 @@ def test_auto_fp64(levels, op):
 
 @pytest.mark.parametrize("levels", LEVELS)
 @pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_plain_fixed_point_fp64(levels, op):
+    """Sweeps in int64 fixed point, one binary scale per pole group."""
+    u = inputs.uniform(levels, 250 + len(levels))
+    assert rel_err(run(u, levels, op, path=gbh.GBH_PATH_PLAIN, arith=2), ORACLE[op](u, levels), u) <= TOL64
+
+
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_plain_fixed_point_wide_range(op):
+    """Pole groups whose values span many binades, and groups of zeros next to
+    groups of tiny values: every group takes its own scale."""
+    levels = (6, 7, 3)
+    rng = np.random.default_rng(9)
+    u = rng.uniform(-1, 1, inputs.num_points(levels)) * 2.0 ** rng.integers(-40, 40, inputs.num_points(levels))
+    u.reshape(9, 129, 65)[:2] *= 1e-300
+    u.reshape(9, 129, 65)[2] = 0.0
+    ref = ORACLE[op](u, levels)
+    got = run(u, levels, op, path=gbh.GBH_PATH_PLAIN, arith=2)
+    assert rel_err(got, ref, u) <= TOL64
+
+
+@pytest.mark.parametrize("levels", LEVELS)
+@pytest.mark.parametrize("op", ["h", "d", "a"])
 @pytest.mark.parametrize("path", [gbh.GBH_PATH_PLAIN, gbh.GBH_PATH_AUTO])
 def test_fp32(levels, op, path):
     u32 = inputs.uniform(levels, 300 + len(levels), dtype=np.float32)
