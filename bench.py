@@ -469,20 +469,25 @@ def run_ours(args):
 
 
 def run_case(args):
-    """One small workload for profilers: `transform:L0,L1,..:op:dtype` or
-    `scheme:d,n:op:dtype` (op h/d/a, dtype f64/f32), run warmup + steps times;
-    prints one JSON line with the median time."""
+    """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith]]`
+    (path auto/plain/fused, arith 0/1/2) or `scheme:d,n:op:dtype` (op h/d/a,
+    dtype f64/f32), run warmup + steps times; prints one JSON line with the
+    median time and the per-kernel launch times of a second, profiled pass."""
     import torch
 
     import paper_1309_0392_gb300 as gbh
-    kind, spec, op, dt = args.case.split(":")
+    from paper_1309_0392_gb300 import _lib
+    kind, spec, op, dt, *extra = args.case.split(":")
+    path = {"auto": gbh.GBH_PATH_AUTO, "plain": gbh.GBH_PATH_PLAIN,
+            "fused": gbh.GBH_PATH_FUSED}[extra[0] if extra else "auto"]
+    arith = int(extra[1]) if len(extra) > 1 else 0
     dtype = torch.float64 if dt == "f64" else torch.float32
     opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}[op]
     gen = torch.Generator(device="cuda").manual_seed(1)
     if kind == "transform":
         levels = tuple(int(v) for v in spec.split(","))
         t = torch.empty(gbh.num_points(levels), dtype=dtype, device="cuda").uniform_(-1, 1, generator=gen)
-        fn = lambda: gbh.transform(t, levels, opc)  # noqa: E731
+        fn = lambda: gbh.transform(t, levels, opc, path=path, arith=arith)  # noqa: E731
         pts = t.numel()
     else:
         d, n = (int(v) for v in spec.split(","))
@@ -495,7 +500,16 @@ def run_case(args):
     for _ in range(args.warmup):
         fn()
     ms = _ms(fn, max(1, args.steps))
-    print(json.dumps({"case": args.case, "ms": ms, "points": pts, "Gpts_s": pts / (ms * 1e-3) / 1e9}), flush=True)
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    for _ in range(max(1, args.steps)):
+        fn()
+    torch.cuda.synchronize()
+    _lib.profile_enable(False)
+    kernels = {k: {"launches": n, "ms_per_launch": t / n, "alg_GB_s": b / (t * 1e-3) / 1e9 if t > 0 else None}
+               for k, (n, t, b) in _lib.profile_read().items()}
+    print(json.dumps({"case": args.case, "ms": ms, "points": pts, "Gpts_s": pts / (ms * 1e-3) / 1e9,
+                      "kernels": kernels}), flush=True)
 
 
 def main():

@@ -5,7 +5,7 @@ baseline leg of ``bench.py`` may import this package.  The GPU library never
 imports it and shares no code with it.
 
 Every array argument is a C-contiguous float64 numpy array in the grid layout
-of the paper's Sec. 3 ("standard row major order", dimension 0 contiguous):
+of Sec. 3 (row-major, dimension 0 contiguous):
 ``u.reshape(n_{d-1}, ..., n_0)`` in numpy terms, ``n_k = 2**levels[k] + 1``.
 """
 from __future__ import annotations

@@ -1192,7 +1192,7 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
     P.g0 = c.g0;
     P.growth_bits = c.growth_bits;
     const double bytes = 2.0 * sizeof(ST) * (double)P.total * c.W;
-    const char *name = cp.mask == 0 ? "fused_class0" : "fused_class1";
+    const char *name = cp.mask == 0 ? "fused_class0" : cp.mask == 1 ? "fused_class1_d0" : cp.mask == 2 ? "fused_class1_d1" : "fused_class1_d2";
 #define GBH_T3_CALL(a, b, cc, m) \
     if (LM == m && E0 == a && E1 == b && E2 == cc) return launch_tile3_shape<ST, FIX, OP, a, b, cc, m>(P, u, st, bytes, name);
     if constexpr (sizeof(ST) == 8) {

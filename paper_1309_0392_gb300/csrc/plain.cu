@@ -1,18 +1,19 @@
-// Plain path: one in-place sweep kernel per dimension, native fp32/fp64
-// arithmetic, in the operation order of the serial algorithm (so fp64 results
-// are bit-identical to a serial run of Alg. 1 in dimension order 0..d-1).
+// Plain path: one in-place sweep kernel per dimension.  With native fp32/fp64
+// arithmetic every point is computed in the operation order of the serial
+// algorithm (so fp64 results are bit-identical to a serial run of Alg. 1 in
+// dimension order 0..d-1); fp64 may instead compute in int64 fixed point.
 //
-//   rows kernel       dimension 0: a CTA stages whole contiguous rows in shared
-//                     memory (coalesced), then every point is computed from
-//                     the staged copy (Sec. 3: "working in direction of the
-//                     data layout vectorization is difficult" -- here the
-//                     staging makes it a plain coalesced stream).
-//   pole kernel       dimensions k >= 1: one thread per pole; neighbouring
-//                     threads own neighbouring poles, which are contiguous in
-//                     memory (Sec. 3, Fig. 3 right: work orthogonal to the
-//                     poles), so every load and store is coalesced.
-//   level kernel      any dimension with few, long poles: one launch per level,
-//                     threads over (pole, point of that level).
+//   pole-group kernel  any dimension whose poles fit in shared memory: a CTA
+//                      stages a group of poles (rows of dimension 0, or
+//                      neighbouring poles of an outer dimension side by side),
+//                      so that every global access is coalesced whichever way
+//                      the poles run through memory (Sec. 3 discusses the
+//                      cost of working along versus across the data layout).
+//   pole kernel        short poles of dimensions k >= 1 (up to 33 points):
+//                      one thread per pole, held in registers; neighbouring
+//                      threads own neighbouring poles (Sec. 3, Fig. 3 right).
+//   level kernel       any dimension with few, long poles: one launch per level,
+//                      threads over (pole, point of that level).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -24,8 +25,6 @@ namespace {
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE, OP_A = GBH_ADJOINT };
 
-constexpr int kRowCapElems = 16385;      // longest row staged in shared memory
-constexpr int kRowChunk = 4096;          // elements staged per CTA for short rows
 constexpr int kRegPoleMaxLevel = 5;      // poles up to 33 points kept in registers
 constexpr int64_t kMinPolesForThreadPerPole = 152 * 64;
 
@@ -127,69 +126,6 @@ __global__ void __launch_bounds__(256) k_pole_global(T *__restrict__ u, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// rows kernel: dimension 0, rows staged in shared memory
-// ---------------------------------------------------------------------------
-
-template <typename T, int OP>
-__global__ void __launch_bounds__(256) k_rows(T *__restrict__ u, int64_t rows, int l, int rows_per_cta)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s = reinterpret_cast<T *>(smem_raw);
-    const int n = (1 << l) + 1;
-    const int64_t row0 = (int64_t)blockIdx.x * rows_per_cta;
-    const int64_t left = rows - row0;
-    const int R = left < rows_per_cta ? (int)left : rows_per_cta;
-    const int64_t base = row0 * n;
-    const int cnt = R * n;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) s[e] = u[base + e];
-    __syncthreads();
-    if (OP == OP_H) {
-        // every surplus from the staged nodal values: one step per point
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const int i = e % n;
-            if (i > 0 && i < n - 1) {
-                const int lb = i & (-i);
-                u[base + e] = s[e] - T(0.5) * (s[e - lb] + s[e + lb]);
-            }
-        }
-    } else if (OP == OP_D) {
-        for (int lev = 1; lev <= l; ++lev) {
-            const int st = 1 << (l - lev);
-            const int per_row = 1 << (lev - 1);
-            const int tot = R * per_row;
-            for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-                const int r = q >> (lev - 1), k = q & (per_row - 1);
-                const int e = r * n + (2 * k + 1) * st;
-                s[e] = s[e] + T(0.5) * (s[e - st] + s[e + st]);
-            }
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const int i = e % n;
-            if (i > 0 && i < n - 1) u[base + e] = s[e];
-        }
-    } else {
-        // gather form of the transpose; contributions are taken coarse to fine,
-        // left before right, as the serial scatter applies them
-        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-            const int i = e % n;
-            T y = s[e];
-            if (i == 0) {
-                for (int t = 1 << (l - 1); t >= 1; t >>= 1) y = y - T(0.5) * s[e + t];
-            } else if (i == n - 1) {
-                for (int t = 1 << (l - 1); t >= 1; t >>= 1) y = y - T(0.5) * s[e - t];
-            } else {
-                for (int t = (i & (-i)) >> 1; t >= 1; t >>= 1) {
-                    y = y - T(0.5) * s[e - t];
-                    y = y - T(0.5) * s[e + t];
-                }
-            }
-            u[base + e] = y;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // level kernel: one launch per level, threads over (pole, point of the level)
 // ---------------------------------------------------------------------------
 
@@ -223,17 +159,44 @@ __global__ void __launch_bounds__(256) k_level(T *__restrict__ u, int64_t S, int
 }
 
 // ---------------------------------------------------------------------------
-// pole-group kernel: a group of neighbouring poles staged in shared memory
+// pole-group kernel: a group of poles staged in shared memory
 // ---------------------------------------------------------------------------
 //
-// G poles of one dimension (length n = 2^l + 1, stride S) per CTA, loaded with
-// neighbouring poles side by side (coalesced), swept level by level in shared
-// memory, written back.  Rows of dimension 0 (S = 1) load row after row.
+// G poles of one dimension (length n = 2^l + 1, stride S) per CTA.  Poles of
+// dimension k >= 1 are loaded side by side (neighbouring poles are contiguous,
+// Sec. 3, Fig. 3 right: work orthogonal to the poles), rows of dimension 0
+// row after row; either way every global access is coalesced, and all loads
+// of the group are in flight at once (cp.async).  Then:
+//   H  every surplus from the staged nodal values in one step (the two
+//      neighbours of a point are always coarser, hence still nodal);
+//   D  level by level, coarse to fine, in shared memory;
+//   A  y[p] = x[p] - 1/2 sum over the children of p: in fixed point every
+//      point at once from the staged values; natively level by level, coarse
+//      to fine, each parent gathering from its two children of that level
+//      (left, then right: the order of the serial scatter).
+// Boundary points are not stored back by H and D (they do not change).
 // FIX (fp64 only): the group is scaled by its largest binary exponent and
-// swept in int64 fixed point (hierarchize exact in the doubling form; the
-// inverse and the transpose add halved sums); one int64 -> fp64 conversion per
-// point instead of two fp64 operations per point.
-constexpr int kGroupElems = 8192;
+// computed in int64 fixed point: H and A exactly (doubling forms 2u - L - R
+// and 2x - sum of children), D with halved sums; one int64 -> fp64 conversion
+// per stored point replaces the fp64 arithmetic.
+constexpr int kGroupElems = 8192;        // elements staged per CTA (target)
+constexpr int kGroupMaxElems = 16385;    // longest pole staged whole
+
+__device__ __forceinline__ void pg_cp8(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void pg_cp4(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void pg_commit_wait()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 __device__ __forceinline__ long long g_to_fixed(long long bits, int emax, int c)
 {
@@ -247,12 +210,15 @@ __device__ __forceinline__ long long g_to_fixed(long long bits, int emax, int c)
     return bits < 0 ? -v : v;
 }
 
-__device__ __forceinline__ double g_from_fixed(long long v, int X)
+// v * 2^X for any X (slow path: exponents near the ends of the range)
+__device__ __noinline__ double g_from_fixed_slow(long long v, int X)
 {
     if (v == 0) return 0.0;
     return ldexp(__ll2double_rn(v), X);
 }
 
+// v * 2^X by adding X to the exponent field; valid while the result stays
+// normal, which the caller guarantees (group exponent in [64, 1900])
 __device__ __forceinline__ double g_from_fixed_fast(long long v, long long Xhi)
 {
     const long long b = __double_as_longlong(__ll2double_rn(v));
@@ -266,86 +232,75 @@ __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S
     using V = typename std::conditional<FIX, long long, T>::type;
     extern __shared__ __align__(16) unsigned char smr[];
     V *sv = reinterpret_cast<V *>(smr);
-    int64_t *pb = reinterpret_cast<int64_t *>(smr + (size_t)kGroupElems * sizeof(V));
     __shared__ int s_emax;
     const int n = (1 << l) + 1, last = 1 << l;
     const int64_t t0 = (int64_t)blockIdx.x * G;
     const int Gc = (poles - t0) < (int64_t)G ? (int)(poles - t0) : G;
     const int cnt = Gc * n;
+    int64_t *pb = reinterpret_cast<int64_t *>(smr + (((size_t)G * n * sizeof(V) + 15) & ~(size_t)15));
     const unsigned magG = Gc == 1 ? 0u : (0xFFFFFFFFu / (unsigned)Gc) + 1u;
-    if (!ROWS)
+    const unsigned magN = (0xFFFFFFFFu / (unsigned)n) + 1u;
+    if (!ROWS) {
         for (int g = threadIdx.x; g < Gc; g += blockDim.x) {
             const int64_t t = t0 + g, o = t / S;
             pb[g] = o * S * n + (t - o * S);
         }
+    }
     if (threadIdx.x == 0) s_emax = 0;
     __syncthreads();
-    // element w of the group: rows go row after row, poles side by side
-    auto gaddr = [&](int w, int &sidx) -> int64_t {
+    // element w of the group (the order of the global accesses): its global
+    // address, its shared-memory slot and its index i along the pole
+    auto locate = [&](int w, int &sidx, int &i) -> int64_t {
         if (ROWS) {
             sidx = w;
+            i = w - (int)__umulhi((unsigned)w, magN) * n;
             return t0 * n + w;
         }
-        const int i = magG ? (int)__umulhi((unsigned)w, magG) : w, g = w - i * Gc;
+        i = magG ? (int)__umulhi((unsigned)w, magG) : w;
+        const int g = w - i * Gc;
         sidx = g * n + i;
         return pb[g] + (int64_t)i * S;
     };
-    int emax = 0;
-    for (int w0 = threadIdx.x; w0 < cnt; w0 += blockDim.x * 4) {
-        T tmp[4];
-        int sid[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int w = w0 + q * blockDim.x;
-            if (w < cnt) tmp[q] = u[gaddr(w, sid[q])];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int w = w0 + q * blockDim.x;
-            if (w < cnt) {
-                if constexpr (FIX) {
-                    const long long bits = __double_as_longlong((double)tmp[q]);
-                    emax = max(emax, (int)((unsigned long long)bits >> 52) & 0x7FF);
-                    sv[sid[q]] = (V)bits;
-                } else {
-                    sv[sid[q]] = (V)tmp[q];
-                }
-            }
-        }
+    for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+        int sidx, i;
+        const int64_t a = locate(w, sidx, i);
+        if constexpr (sizeof(T) == 8) pg_cp8(sv + sidx, u + a);
+        else pg_cp4(sv + sidx, u + a);
     }
+    pg_commit_wait();
+    __syncthreads();
+
     int X = 0;
     long long Xhi = 0;
     bool fast = true;
     if constexpr (FIX) {
-        emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+        int emax = 0;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x)
+            emax = max(emax, (int)((unsigned long long)sv[e] >> 52) & 0x7FF);
+        emax = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
         if ((threadIdx.x & 31) == 0) atomicMax(&s_emax, emax);
         __syncthreads();
         emax = s_emax;
         const int c = g0 - 53;
-        X = emax - 1075 - c - (OP == OP_H ? 1 : 0);
+        X = emax - 1075 - c - (OP == OP_D ? 0 : 1);    // H and A: doubled results
         Xhi = (long long)X << 52;
         fast = emax >= 64 && emax <= 1900;
         for (int e = threadIdx.x; e < cnt; e += blockDim.x) sv[e] = g_to_fixed((long long)sv[e], emax, c);
+        __syncthreads();
     }
-    __syncthreads();
-    // level-ordered sweeps, all poles of the group at once
+    auto put = [&](int64_t a, V y) {
+        if constexpr (FIX) u[a] = fast ? g_from_fixed_fast(y, Xhi) : g_from_fixed_slow(y, X);
+        else u[a] = y;
+    };
     if (OP == OP_H) {
-        for (int lev = l; lev >= 1; --lev) {
-            const int s = 1 << (l - lev), per = 1 << (lev - 1);
-            for (int q = threadIdx.x; q < Gc * per; q += blockDim.x) {
-                const int r = q >> (lev - 1), i = (2 * (q & (per - 1)) + 1) * s;
-                V *row = sv + r * n;
-                if constexpr (FIX) row[i] = (row[i] + row[i]) - row[i - s] - row[i + s];
-                else row[i] = row[i] - V(0.5) * (row[i - s] + row[i + s]);
-            }
-            __syncthreads();
-        }
-        if constexpr (FIX) {
-            for (int r = threadIdx.x; r < Gc; r += blockDim.x) {
-                sv[r * n] += sv[r * n];
-                sv[r * n + last] += sv[r * n + last];
-            }
-            __syncthreads();
+        for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+            int sidx, i;
+            const int64_t a = locate(w, sidx, i);
+            if (i == 0 || i == last) continue;
+            const int s = i & (-i);
+            const V *p = sv + sidx;
+            if constexpr (FIX) put(a, (p[0] + p[0]) - p[-s] - p[s]);
+            else put(a, p[0] - V(0.5) * (p[-s] + p[s]));
         }
     } else if (OP == OP_D) {
         for (int lev = 1; lev <= l; ++lev) {
@@ -358,32 +313,48 @@ __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S
             }
             __syncthreads();
         }
+        for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+            int sidx, i;
+            const int64_t a = locate(w, sidx, i);
+            if (i == 0 || i == last) continue;
+            put(a, sv[sidx]);
+        }
+    } else if constexpr (FIX) {
+        // every point at once from the staged values (exact):
+        // 2 y[p] = 2 x[p] - sum_{t < lowbit(p)} (x[p - t] + x[p + t])
+        for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+            int sidx, i;
+            const int64_t a = locate(w, sidx, i);
+            const V *p = sv + sidx;
+            const int top = (i == 0 || i == last) ? (last >> 1) : ((i & (-i)) >> 1);
+            V y = p[0] + p[0];
+            for (int t = top; t >= 1; t >>= 1) {
+                if (i != 0) y -= p[-t];
+                if (i != last) y -= p[t];
+            }
+            put(a, y);
+        }
     } else {
-        // transpose: level by level coarse to fine, every parent p = 2 s q
-        // collects its two children of this level (left, then right)
+        // level by level, coarse to fine: the parents p = 2 s q of level-lev
+        // children take their contributions (left, then right); a child's own
+        // value changes only at finer levels, so it is still x when read
         for (int lev = 1; lev <= l; ++lev) {
             const int s = 1 << (l - lev), per = (1 << (lev - 1)) + 1;
             for (int w = threadIdx.x; w < Gc * per; w += blockDim.x) {
                 const int r = w / per, q = w - r * per, p = 2 * s * q;
                 V *row = sv + r * n;
-                if constexpr (FIX) {
-                    const V lc = q > 0 ? row[p - s] : V(0), rc = q < per - 1 ? row[p + s] : V(0);
-                    row[p] = row[p] - ((lc + rc) >> 1);
-                } else {
-                    V y = row[p];
-                    if (q > 0) y = y - V(0.5) * row[p - s];
-                    if (q < per - 1) y = y - V(0.5) * row[p + s];
-                    row[p] = y;
-                }
+                V y = row[p];
+                if (q > 0) y = y - V(0.5) * row[p - s];
+                if (q < per - 1) y = y - V(0.5) * row[p + s];
+                row[p] = y;
             }
             __syncthreads();
         }
-    }
-    for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
-        int sidx;
-        const int64_t a = gaddr(w, sidx);
-        if constexpr (FIX) u[a] = fast ? (T)g_from_fixed_fast((long long)sv[sidx], Xhi) : (T)g_from_fixed((long long)sv[sidx], X);
-        else u[a] = (T)sv[sidx];
+        for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+            int sidx, i;
+            const int64_t a = locate(w, sidx, i);
+            put(a, sv[sidx]);
+        }
     }
 }
 
@@ -446,15 +417,16 @@ int launch_group(T *u, const Geom &g, int k, cudaStream_t st)
     const int64_t blocks = (poles + G - 1) / G;
     if (blocks > INT32_MAX) return GBH_ERANGE;
     using V = typename std::conditional<FIX, long long, T>::type;
-    const size_t smem = (size_t)kGroupElems * sizeof(V) + (size_t)G * sizeof(int64_t) + 16;
+    const size_t smem = (((size_t)G * n * sizeof(V) + 15) & ~(size_t)15) + (ROWS ? 0 : (size_t)G * sizeof(int64_t));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_pole_group<T, OP, FIX, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kGroupElems * sizeof(long long) + kGroupElems * sizeof(int64_t) + 16));
+                             (int)((kGroupMaxElems + kGroupElems / 3 + 4) * sizeof(long long)));
         attr = true;
     }
-    // fixed point headroom: hierarchize doubles once; the inverse grows by at
-    // most l + 1 (sum of hat weights); the transpose by at most l + 1
+    // fixed-point headroom below 2^63: H doubles once (|2u - L - R| <= 4 max);
+    // D grows by at most l + 1 (hat weights along a pole sum to at most l + 1);
+    // A sums at most 2 l children besides the doubled point
     const int g0 = OP == OP_H ? 59 : 59 - (int)std::ceil(std::log2((double)l + 1.0));
     ProfScope ps(ROWS ? "plain_rows_group" : "plain_pole_group", st, 2.0 * sizeof(T) * (double)g.total);
     k_pole_group<T, OP, FIX, ROWS><<<(unsigned)blocks, 256, smem, st>>>(u, g.S[k], poles, l, G, g0);
@@ -468,31 +440,12 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
 {
     const int l = g.l[k];
     const int64_t poles = g.total / g.n[k];
-    if constexpr (sizeof(T) == 8) {
-        if (fixed && g.n[k] <= kGroupElems) {
-            if (k == 0) return launch_group<T, OP, true, true>(u, g, k, st);
-            return launch_group<T, OP, true, false>(u, g, k, st);
-        }
-    }
+    const bool fix = sizeof(T) == 8 && fixed;
     if (k == 0) {
-        if (g.n[0] > kRowCapElems) return sweep_level<T, OP>(u, g, 0, st);
-        const int n = (int)g.n[0];
-        const int rpc = std::max(1, kRowChunk / n);
-        const int64_t blocks = (poles + rpc - 1) / rpc;
-        const size_t smem = (size_t)rpc * n * sizeof(T);
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_rows<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kRowCapElems * (int)sizeof(double));
-            attr_set = true;
-        }
-        if (blocks > INT32_MAX) return GBH_ERANGE;
-        ProfScope ps("plain_rows", st, 2.0 * sizeof(T) * (double)g.total);
-        k_rows<T, OP><<<(unsigned)blocks, 256, smem, st>>>(u, poles, l, rpc);
-        ps.done();
-        count_launches(1);
-        return check_launch();
+        if (g.n[0] > kGroupMaxElems) return sweep_level<T, OP>(u, g, 0, st);
+        return fix ? launch_group<T, OP, sizeof(T) == 8, true>(u, g, 0, st) : launch_group<T, OP, false, true>(u, g, 0, st);
     }
+    if (fix && g.n[k] <= kGroupElems) return launch_group<T, OP, sizeof(T) == 8, false>(u, g, k, st);
     if (l <= kRegPoleMaxLevel) {
         switch (l) {
             case 1: return launch_pole_regs<T, OP, 1>(u, g.S[k], poles, st);
