@@ -2,20 +2,22 @@
 // persistent kernel driven by a device work queue, and the fp64 gather of the
 // hierarchical surpluses into the sparse grid.
 //
-// Work items.  Each grid runs through phases: an exponent scan (fp64 only),
-// then one sweep per dimension.  Items are (grid, phase, range of rows or
-// poles) and are handed out by an atomic ticket in a fixed order: grids are
-// grouped into waves that fit in L2 together, and within a wave the items run
-// phase-major, so phase k+1 of a grid mostly reads phase k's output from L2.
-// An item of phase p waits (bounded spin) until every item of phase p-1 of its
-// grid has finished; tickets are taken in order by resident CTAs, so every
-// dependency is already owned by a running CTA.
+// Work items.  Each grid runs through phases; items are (grid, phase, tile)
+// and are handed out by an atomic ticket in a fixed order: grids are grouped
+// into waves that fit in L2 together, and within a wave the items run
+// phase-major, so phase p+1 of a grid mostly reads phase p's output from L2.
+// An item of phase p waits (bounded spin) until every item of the previous
+// phase of its grid has finished; tickets are taken in order by resident
+// CTAs, so every dependency is already owned by a running CTA.
 //
-// Arithmetic.  fp32 grids compute in fp32.  fp64 grids compute in exact int64
-// fixed point held in place between phases (the same 8 bytes per point): the
-// scan finds the grid's largest binary exponent, the first sweep converts,
-// the last sweep converts back.  Hierarchization uses the doubling form
-// 2u - L - R, so it rounds only once, at the final conversion.
+// Two kernels share this queue.  k_fused (plans): a phase is a group of
+// consecutive dimensions whose pole sets fit in one shared-memory tile, so a
+// grid crosses memory once per group; fp64 tiles compute in exact int64 fixed
+// point with their own binary scale.  k_batched (the allocation-free entry
+// point): one phase per dimension, with a per-grid exponent scan and int64
+// fixed point held in place between phases (the same 8 bytes per point); the
+// first sweep converts, the last converts back.  Either way hierarchization
+// uses the doubling form 2u - L - R, so it rounds once per stored value.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -34,7 +36,11 @@ constexpr double kWaveBytes = 16.0 * 1024 * 1024;
 constexpr long long kSpinLimit = 1ll << 24;   // bounded waits (~ seconds)
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
-enum ItemKind { K_SCAN = 0, K_CONV_IN = 1, K_CONV_OUT = 2, K_ROWS = 3, K_POLES = 4, K_GROUP = 5, K_LATT = 6 };
+enum ItemKind {
+    K_SCAN = 0, K_CONV_IN = 1, K_CONV_OUT = 2, K_ROWS = 3, K_POLES = 4, K_GROUP = 5, K_LATT = 6,
+    K_FUSED = 7,         // tile of pole sets of a dimension group (fused kernel)
+    K_LATT_NAT = 8       // coarse lattice of a split dimension, native arithmetic (fused kernel)
+};
 
 // t / S as __umul64hi(t, ceil(2^64 / S)), exact for t < 2^64 / S; S = 1 is
 // marked by m = 0.
@@ -62,7 +68,11 @@ struct GridInfo {
     int g0;              // fixed point: input scale bits (per op)
     int g0_d;
     int passes;          // dimensions with a sweep
-    int pad;
+    int ngroups;         // dimension groups of the fused kernel
+    signed char grp_lo[kPlanMaxD];     // group q covers dimensions grp_lo..grp_hi
+    signed char grp_hi[kPlanMaxD];
+    signed char grp_m[kPlanMaxD];      // block level of a split dimension (-1: whole poles)
+    signed char grp_g0[2][kPlanMaxD];  // fixed-point input scale bits (hierarchize, inverse)
 };
 
 struct Item {
@@ -142,6 +152,8 @@ struct BatchParams {
     int *status;
     int op;
     long long spin_limit;   // bounded waits: polls before giving up
+    int stall_grid;         // test hook: every item of this grid waits on a
+                            // dependency that nothing releases (-1: none)
 };
 
 // Phases of a grid: 0 exponent scan and 1 conversion to fixed point (fp64
@@ -151,6 +163,7 @@ constexpr int kPhases = 3 + 2 * kPlanMaxD;
 constexpr int kPhaseOut = kPhases - 1;
 constexpr int kGroupLevel = 12;                  // block level of long dimensions
 constexpr int kGroupElems = 8208;               // shared-memory elements per item
+constexpr int kSplitLevel = 13;                  // block level of dimensions longer than a tile (fused kernel)
 
 template <int OP>
 __device__ __forceinline__ long long fx_op(long long v, long long L, long long R)
@@ -308,6 +321,41 @@ __device__ __forceinline__ void stream_elems(int64_t count, Src src, Dst dst)
     }
 }
 
+// Thread 0 takes the next ticket and waits (bounded) until the item's
+// dependency -- every item of the previous phase of its grid -- has finished.
+// Returns the item index, or -1 when the queue is empty, the wait gave up
+// (status GBH_ETIMEOUT) or another CTA reported an error.  Every thread of
+// the CTA calls it.
+__device__ __forceinline__ int next_item(const BatchParams &P, int *s_item, int *s_abort)
+{
+    if (threadIdx.x == 0) {
+        *s_item = (int)atomicAdd(P.ticket, 1u);
+        *s_abort = 0;
+        if (*s_item < P.nitems) {
+            const Item it = P.items[*s_item];
+            int wait = it.wait, want = 0;
+            if (it.grid == P.stall_grid) {
+                wait = kPhaseOut;
+                want = 0x7FFFFFFF;
+            } else if (wait >= 0) {
+                want = P.need[it.grid * kPhases + wait];
+            }
+            if (wait >= 0) {
+                const int *cnt = P.done + it.grid * kPhases + wait;
+                long long spins = 0;
+                while (ld_acquire(cnt) < want) {
+                    if (++spins > P.spin_limit) { atomicExch(P.status, GBH_ETIMEOUT); *s_abort = 1; break; }
+                    __nanosleep(64);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int idx = *s_item;
+    if (idx >= P.nitems || *s_abort || ld_acquire(P.status) != 0) return -1;
+    return idx;
+}
+
 template <typename ST, int OP>
 __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
 {
@@ -319,25 +367,8 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
     V *sv = reinterpret_cast<V *>(sm);
 
     for (;;) {
-        if (tid == 0) {
-            s_item = (int)atomicAdd(P.ticket, 1u);
-            s_abort = 0;
-            if (s_item < P.nitems) {
-                const Item it = P.items[s_item];
-                if (it.wait >= 0) {
-                    const int *cnt = P.done + it.grid * kPhases + it.wait;
-                    const int want = P.need[it.grid * kPhases + it.wait];
-                    long long spins = 0;
-                    while (ld_acquire(cnt) < want) {
-                        if (++spins > P.spin_limit) { atomicExch(P.status, GBH_ETIMEOUT); s_abort = 1; break; }
-                        __nanosleep(64);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const int idx = s_item;
-        if (idx >= P.nitems || s_abort || ld_acquire(P.status) != 0) return;
+        const int idx = next_item(P, &s_item, &s_abort);
+        if (idx < 0) return;
         const Item it = P.items[idx];
         const GridInfo &gi = P.grids[it.grid];
         ST *sbase = reinterpret_cast<ST *>(P.ptrs[it.grid]);
@@ -445,6 +476,350 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batched(const BatchParams P)
             atomicAdd(P.done + it.grid * kPhases + it.phase, 1);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// fused kernel: dimension groups staged in shared memory
+// ---------------------------------------------------------------------------
+//
+// The plan's kernel.  A grid's dimensions are cut into groups of consecutive
+// dimensions whose pole sets (every point of the group's dimensions, the
+// other coordinates fixed) fit in one tile; a dimension longer than a tile is
+// a group of its own, split into blocks of 2^13 + 1 points and the coarse
+// lattice of the block ends (hierarchize: blocks, then lattice; the inverse:
+// lattice first).  An item is a tile of pole sets: loaded, transformed along
+// every dimension of its group in shared memory, stored, so a grid crosses
+// memory once per group instead of once per dimension plus conversions.
+// fp64 computes in int64 fixed point with the tile's own binary scale (exact
+// for the hierarchization, one rounding per point at the store); lattice
+// items, a few points per pole, compute natively.
+
+// Poles of one dimension of a tile.  Element i of pole set g sits at
+// sv[g sG + i sI]: pole sets one after another (sG = M, sI = 1) when their
+// points are contiguous in memory, side by side (sG = 1, sI = Gc) when pole
+// sets are strided -- either way shared memory follows the order of the
+// global accesses.  The dimension has local stride sk (product of the extents
+// of the group's lower dimensions) and extent nk, so pole (g, a, b) holds the
+// points i = a + sk (j + nk b), j = 0..nk-1.  Poles are numbered so that
+// neighbouring threads touch neighbouring words.
+struct TilePoles {
+    int Gc, pps, sk, nk, sG, sI;
+    bool gfast;
+    unsigned magA, magK;
+
+    __device__ __forceinline__ int base(int p) const
+    {
+        int g, r;
+        if (gfast) {
+            r = magA ? (int)__umulhi((unsigned)p, magA) : p;
+            g = p - r * Gc;
+        } else {
+            g = magA ? (int)__umulhi((unsigned)p, magA) : p;
+            r = p - g * pps;
+        }
+        const int b = magK ? (int)__umulhi((unsigned)r, magK) : r;
+        const int a = r - b * sk;
+        return g * sG + (a + b * sk * nk) * sI;
+    }
+};
+
+// x / dv as __umulhi(x, magic), exact for x * dv < 2^32; dv = 1 gives 0
+__host__ __device__ __forceinline__ unsigned magic_u32(int dv)
+{
+    return dv == 1 ? 0u : (0xFFFFFFFFu / (unsigned)dv) + 1u;
+}
+
+// Short poles (level L <= 5): one thread per pole, held in registers.  CONV
+// converts the staged fp64 bits to fixed point on the way in.
+template <typename V, int L, int OP, bool CONV>
+__device__ __forceinline__ void tile_regs(V *sv, const TilePoles &tp, int poles, int emax, int c)
+{
+    constexpr int n = (1 << L) + 1;
+    const int st = tp.sk * tp.sI;
+    for (int p = threadIdx.x; p < poles; p += blockDim.x) {
+        V *q = sv + tp.base(p);
+        V v[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            V x = q[i * st];
+            if constexpr (CONV) x = (V)b_to_fixed_fast(__longlong_as_double((long long)x), emax, c);
+            v[i] = x;
+        }
+        b_pole_regs<V, L, OP>(v);
+#pragma unroll
+        for (int i = 0; i < n; ++i) q[i * st] = v[i];
+    }
+}
+
+template <typename V, int OP, bool CONV>
+__device__ __forceinline__ void tile_regs_dispatch(int L, V *sv, const TilePoles &tp, int poles, int emax, int c)
+{
+    switch (L) {
+        case 1: tile_regs<V, 1, OP, CONV>(sv, tp, poles, emax, c); break;
+        case 2: tile_regs<V, 2, OP, CONV>(sv, tp, poles, emax, c); break;
+        case 3: tile_regs<V, 3, OP, CONV>(sv, tp, poles, emax, c); break;
+        case 4: tile_regs<V, 4, OP, CONV>(sv, tp, poles, emax, c); break;
+        default: tile_regs<V, 5, OP, CONV>(sv, tp, poles, emax, c); break;
+    }
+}
+
+// Long poles: level by level in shared memory (hierarchize fine to coarse: a
+// point's two parents are coarser, hence still nodal; the inverse coarse to
+// fine); fixed point doubles the two ends of every pole too.  With enough
+// poles one warp takes a pole (warp-level barriers only), otherwise the whole
+// CTA sweeps every pole level by level.
+template <typename V, int OP>
+__device__ __forceinline__ void tile_long(V *sv, const TilePoles &tp, int poles, int lk)
+{
+    const int st = tp.sk * tp.sI, last = 1 << lk;
+    constexpr bool kEnds = OP == OP_H && std::is_same<V, long long>::value;
+    if (poles >= 2 * (int)(blockDim.x >> 5)) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int p = warp; p < poles; p += nw) {
+            V *q = sv + tp.base(p);
+            for (int step = 1; step <= lk; ++step) {
+                const int lev = OP == OP_H ? lk + 1 - step : step;
+                const int s = 1 << (lk - lev), per = 1 << (lev - 1);
+                for (int j = lane; j < per; j += 32) {
+                    const int i = (2 * j + 1) * s;
+                    q[i * st] = any_op<OP>(q[i * st], q[(i - s) * st], q[(i + s) * st]);
+                }
+                __syncwarp();
+            }
+            if constexpr (kEnds) {
+                if (lane < 2) q[lane * last * st] += q[lane * last * st];
+                __syncwarp();
+            }
+        }
+        return;
+    }
+    const unsigned magP = magic_u32(poles);
+    for (int step = 1; step <= lk; ++step) {
+        const int lev = OP == OP_H ? lk + 1 - step : step;
+        const int s = 1 << (lk - lev), per = 1 << (lev - 1);
+        const int tot = poles * per;
+        for (int w = threadIdx.x; w < tot; w += blockDim.x) {
+            const int pi = magP ? (int)__umulhi((unsigned)w, magP) : w;
+            V *q = sv + tp.base(w - pi * poles);
+            const int i = (2 * pi + 1) * s;
+            q[i * st] = any_op<OP>(q[i * st], q[(i - s) * st], q[(i + s) * st]);
+        }
+        __syncthreads();
+    }
+    if constexpr (kEnds) {
+        for (int w = threadIdx.x; w < 2 * poles; w += blockDim.x) {
+            V *q = sv + tp.base(w >> 1) + (w & 1) * last * st;
+            q[0] += q[0];
+        }
+    }
+}
+
+// One K_FUSED item: `count` pole sets of group q starting at pole set
+// `start` (block `blk` of a split dimension).
+template <typename ST, int OP>
+__device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, ST *sbase, unsigned char *sm,
+                                           int *s_em)
+{
+    using V = typename std::conditional<sizeof(ST) == 8, long long, ST>::type;
+    V *sv = reinterpret_cast<V *>(sm);
+    V *base = reinterpret_cast<V *>(sbase);
+    const int tid = threadIdx.x;
+    const int q = it.dim, lo = gi.grp_lo[q], hi = gi.grp_hi[q], m = gi.grp_m[q];
+    const bool split = m >= 0;
+    int M = 1, pdims = 0;
+    for (int k = lo; k <= hi; ++k) {
+        M *= (1 << gi.l[k]) + 1;
+        pdims += gi.l[k] > 0;
+    }
+    const int64_t Sa = gi.S[lo], Sout = Sa * M;    // Sout: stride of dimension hi + 1
+    if (split) M = (1 << m) + 1;
+    const int Gc = (int)it.count;
+    const int cnt = Gc * M;
+    const bool contig = Sa == 1 && !split;
+    const unsigned magG = magic_u32(Gc), magM = magic_u32(M);
+    int64_t *pb = reinterpret_cast<int64_t *>(sm + (size_t)kGroupElems * sizeof(V));
+    if (!contig) {
+        const int64_t boff = split ? ((int64_t)it.blk << m) * Sa : 0;
+        for (int g = tid; g < Gc; g += blockDim.x) {
+            const int64_t t = it.start + g, o = fdiv(t, gi.divS[lo]);
+            pb[g] = o * Sout + (t - o * Sa) + boff;
+        }
+        __syncthreads();
+    }
+    const int64_t cbase = it.start * M;
+    // global address of element w of the tile (its shared-memory slot is w)
+    // and its index i within the pole set
+    auto gaddr = [&](int w, int &i) -> int64_t {
+        if (contig) {
+            i = 0;
+            return cbase + w;
+        }
+        if (Sa == 1) {
+            const int g = magM ? (int)__umulhi((unsigned)w, magM) : w;
+            i = w - g * M;
+            return pb[g] + i;
+        }
+        i = magG ? (int)__umulhi((unsigned)w, magG) : w;
+        return pb[w - i * Gc] + (int64_t)i * Sa;
+    };
+    // every load of the tile in flight at once.  Other CTAs wrote this grid's
+    // previous phase; the dependency wait (an acquire at gpu scope, then the
+    // CTA barrier) orders their released stores before these loads.
+    for (int w = tid; w < cnt; w += blockDim.x) {
+        int i;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sv + w);
+        const V *src = base + gaddr(w, i);
+        if constexpr (sizeof(V) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    int X = 0, emax = 0, c = 0;
+    bool fast = true, conv = false;
+    int first = lo;
+    while (gi.l[first] == 0) ++first;
+    const int lfirst = split ? m : gi.l[first];
+    if constexpr (sizeof(ST) == 8) {
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const int ex = (int)((sv[e] >> 52) & 0x7FF);
+            emax = ex > emax ? ex : emax;
+        }
+        emax = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
+        if ((tid & 31) == 0) atomicMax(s_em, emax);
+        __syncthreads();
+        emax = *s_em;
+        c = gi.grp_g0[OP == OP_H ? 0 : 1][q] - 53;
+        X = emax - 1075 - c - (OP == OP_H ? pdims : 0);
+        fast = emax >= 64 && emax <= 1900;
+        conv = true;
+        // the conversion rides on the first sweep when that one keeps its
+        // poles in registers
+        if (!fast || lfirst > 5) {
+            for (int e = tid; e < cnt; e += blockDim.x) {
+                const double x = __longlong_as_double((long long)sv[e]);
+                sv[e] = (V)(fast ? b_to_fixed_fast(x, emax, c) : b_to_fixed_slow(x, emax, c));
+            }
+            conv = false;
+            __syncthreads();
+        }
+    }
+    TilePoles tp;
+    tp.Gc = Gc;
+    tp.gfast = Sa > 1;
+    tp.sG = tp.gfast ? 1 : M;
+    tp.sI = tp.gfast ? Gc : 1;
+    tp.sk = 1;
+    for (int k = lo; k <= hi; ++k) {
+        const int lk = split ? m : gi.l[k];
+        tp.nk = (1 << lk) + 1;
+        if (lk > 0) {
+            tp.pps = M / tp.nk;
+            tp.magA = magic_u32(tp.gfast ? Gc : tp.pps);
+            tp.magK = magic_u32(tp.sk);
+            const int poles = Gc * tp.pps;
+            if (lk <= 5) {
+                if (conv) tile_regs_dispatch<V, OP, sizeof(ST) == 8>(lk, sv, tp, poles, emax, c);
+                else tile_regs_dispatch<V, OP, false>(lk, sv, tp, poles, emax, c);
+            } else {
+                tile_long<V, OP>(sv, tp, poles, lk);
+            }
+            conv = false;
+            __syncthreads();
+        }
+        tp.sk *= tp.nk;
+    }
+    // a split dimension's block ends belong to the lattice: not stored
+    for (int w = tid; w < cnt; w += blockDim.x) {
+        int i;
+        const int64_t a = gaddr(w, i);
+        if (split && (i == 0 || i == M - 1)) continue;
+        if constexpr (sizeof(ST) == 8) {
+            const long long v = (long long)sv[w];
+            const double r = fast ? b_from_fixed_fast(v, X) : b_from_fixed_slow(v, X);
+            __stcg(base + a, (V)__double_as_longlong(r));
+        } else {
+            __stcg(base + a, sv[w]);
+        }
+    }
+}
+
+template <typename ST, int OP>
+__global__ void __launch_bounds__(kBThreads, 2) k_fused(const BatchParams P)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    __shared__ int s_abort;
+    __shared__ int s_em;
+    for (;;) {
+        if (threadIdx.x == 0) s_em = 0;
+        const int idx = next_item(P, &s_item, &s_abort);
+        if (idx < 0) return;
+        const Item it = P.items[idx];
+        const GridInfo &gi = P.grids[it.grid];
+        ST *sbase = reinterpret_cast<ST *>(P.ptrs[it.grid]);
+        if (it.kind == K_FUSED) {
+            fused_item<ST, OP>(it, gi, sbase, sm, &s_em);
+        } else {
+            // coarse lattice of a split dimension: points a 2^m, stride 2^m S
+            const int k = gi.grp_lo[it.dim], l = gi.l[k], m = gi.grp_m[it.dim];
+            const int64_t n = ((int64_t)1 << l) + 1, S = gi.S[k];
+            const int L = l - m;    // at most 17 - kSplitLevel
+            const int64_t st = S << m;
+            if (L == 1) b_poles_regs<ST, 1, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
+            else if (L == 2) b_poles_regs<ST, 2, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
+            else if (L == 3) b_poles_regs<ST, 3, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
+            else if (L == 4) b_poles_regs<ST, 4, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(P.done + it.grid * kPhases + it.phase, 1);
+        }
+    }
+}
+
+
+// Items of the fused kernel for one grid and phase: group q runs in phases
+// 2 + 2q (+1 for the second part of a split dimension).
+template <typename Push>
+bool emit_fused_items(const GridInfo &gi, int op, int phase, int64_t chunk, Push push)
+{
+    if (phase < 2 || phase == kPhaseOut) return true;
+    const int q = (phase - 2) / 2, sub = (phase - 2) % 2;
+    if (q >= gi.ngroups) return true;
+    const int lo = gi.grp_lo[q], hi = gi.grp_hi[q], m = gi.grp_m[q];
+    int64_t M = 1;
+    int pdims = 0;
+    for (int k = lo; k <= hi; ++k) {
+        M *= ((int64_t)1 << gi.l[k]) + 1;
+        pdims += gi.l[k] > 0;
+    }
+    if (pdims == 0) return true;
+    const int64_t sets = gi.N / M;
+    if (m < 0) {
+        if (sub) return true;
+        const int64_t G = std::max<int64_t>(1, kGroupElems / M);
+        for (int64_t t = 0; t < sets; t += G)
+            if (!push(K_FUSED, q, t, std::min(G, sets - t), 0)) return false;
+        return true;
+    }
+    // split dimension: hierarchize blocks then lattice, the inverse the reverse
+    const int l = gi.l[lo];
+    const bool blocks_now = (op == GBH_HIERARCHIZE) == (sub == 0);
+    if (!blocks_now) {
+        const int64_t ppi = std::max<int64_t>(kBThreads, chunk >> (l - m));
+        for (int64_t t = 0; t < sets; t += ppi)
+            if (!push(K_LATT_NAT, q, t, std::min(ppi, sets - t), 0)) return false;
+        return true;
+    }
+    const int64_t G = std::max<int64_t>(1, kGroupElems / (((int64_t)1 << m) + 1));
+    for (int64_t a = 0; a < ((int64_t)1 << (l - m)); ++a)
+        for (int64_t t = 0; t < sets; t += G)
+            if (!push(K_FUSED, q, t, std::min(G, sets - t), (int)a)) return false;
+    return true;
 }
 
 // Work items of one grid and phase, in the order they are handed out.  `push`
@@ -571,6 +946,48 @@ double dgrowth(int lev)
     return best;
 }
 
+// Dimension groups of the fused kernel: consecutive dimensions whose pole
+// sets (product of their extents) fit in one tile, greedily from dimension 0;
+// a dimension longer than a tile is a group of its own, split at block level
+// kSplitLevel.  Fixed-point scales: hierarchization grows by at most 4 per
+// swept dimension (doubling form), the inverse by the largest sum of hat
+// weights along a pole per swept dimension.
+static_assert(((1 << kSplitLevel) + 1) <= kGroupElems, "a block must fit in a tile");
+static_assert(kGroupLevel + 5 - kSplitLevel <= 4, "the fused kernel's lattice poles have at most 4 levels");
+
+void make_groups(GridInfo &gi, int d)
+{
+    int q = 0;
+    auto ext = [&](int k) { return ((int64_t)1 << gi.l[k]) + 1; };
+    for (int k = 0; k < d;) {
+        int hi = k, m = -1;
+        int64_t M = ext(k);
+        if (M > kGroupElems) {
+            m = kSplitLevel;
+        } else {
+            while (hi + 1 < d && M * ext(hi + 1) <= kGroupElems) {
+                ++hi;
+                M *= ext(hi);
+            }
+        }
+        int pdims = 0;
+        double growth = 1.0;
+        for (int j = k; j <= hi; ++j)
+            if (gi.l[j] > 0) {
+                ++pdims;
+                growth *= dgrowth(m >= 0 ? m : gi.l[j]);
+            }
+        gi.grp_lo[q] = (signed char)k;
+        gi.grp_hi[q] = (signed char)hi;
+        gi.grp_m[q] = (signed char)m;
+        gi.grp_g0[0][q] = (signed char)(62 - 2 * pdims);
+        gi.grp_g0[1][q] = (signed char)(61 - (int)std::ceil(std::log2(growth) + 1e-9));
+        ++q;
+        k = hi + 1;
+    }
+    gi.ngroups = q;
+}
+
 }  // namespace
 }  // namespace gbh
 
@@ -640,7 +1057,7 @@ int upload(T **dst, const std::vector<T> &src)
 // independent while a few waves stay resident in L2.
 template <typename Push>
 bool order_items(const GridInfo *info, int ngrids, int d, int dtype, int op, int64_t chunk, double wave_bytes,
-                 int *order, int *wave_of, int *prev, int *need, Push push)
+                 bool fused, int *order, int *wave_of, int *prev, int *need, Push push)
 {
     const int es = dtype == GBH_F64 ? 8 : 4;
     for (int g = 0; g < ngrids; ++g) order[g] = g;
@@ -673,12 +1090,13 @@ bool order_items(const GridInfo *info, int ngrids, int d, int dtype, int op, int
                 if (info[g].first_dim < 0) continue;
                 int cnt = 0;
                 const int wait = prev[i];
-                const bool ok = emit_items(info[g], d, dtype, op, ph, chunk,
-                                           [&](int kind, int dim, int64_t st, int64_t c, int blk) {
-                                               if (!push(Item{g, ph, kind, dim, st, c, wait, blk})) return false;
-                                               ++cnt;
-                                               return true;
-                                           });
+                auto put = [&](int kind, int dim, int64_t st, int64_t c, int blk) {
+                    if (!push(Item{g, ph, kind, dim, st, c, wait, blk})) return false;
+                    ++cnt;
+                    return true;
+                };
+                const bool ok = fused ? emit_fused_items(info[g], op, ph, chunk, put)
+                                      : emit_items(info[g], d, dtype, op, ph, chunk, put);
                 if (!ok) return false;
                 need[(size_t)g * kPhases + ph] = cnt;
                 if (cnt > 0) prev[i] = ph;
@@ -693,7 +1111,7 @@ int build_items(gbh_plan *p, int op, std::vector<Item> &items, std::vector<int> 
     need.assign((size_t)p->ngrids * kPhases, 0);
     items.clear();
     std::vector<int> order(p->ngrids), wave(p->ngrids), prev(p->ngrids);
-    order_items(p->info.data(), p->ngrids, p->d, p->dtype, op, kItemPoints, kWaveBytes, order.data(), wave.data(),
+    order_items(p->info.data(), p->ngrids, p->d, p->dtype, op, kItemPoints, kWaveBytes, true, order.data(), wave.data(),
                 prev.data(), need.data(), [&](const Item &it) {
                     items.push_back(it);
                     return true;
@@ -733,6 +1151,7 @@ int finish_plan(gbh_plan *p)
         gi.passes = passes;
         gi.g0 = 61 - 2 * passes;
         gi.g0_d = 61 - (int)std::ceil(std::log2(growth) + 1e-9);
+        make_groups(gi, d);
         p->total_points += N;
     }
     for (int o = 0; o < 2; ++o) {
@@ -967,15 +1386,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.need = plan->d_need[op];
     P.op = op;
     P.spin_limit = plan->spin_limit;
-    if (plan->stall_grid >= 0) {
-        // every phase of the chosen grid waits for one item more than exists
-        std::vector<int> need = plan->need[op];
-        for (int ph = 0; ph < kPhases; ++ph) need[(size_t)plan->stall_grid * kPhases + ph] += 1;
-        if (cudaMemcpyAsync(plan->d_need[op], need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess)
-            return GBH_ECUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
-    }
+    P.stall_grid = plan->stall_grid;
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
     const size_t smem = kGroupElems * es + kGroupElems * sizeof(int64_t) / 2;
     auto launch = [&](auto kern) -> int {
@@ -991,8 +1402,8 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
         return check_launch();
     };
     if (plan->dtype == GBH_F64)
-        return op == GBH_HIERARCHIZE ? launch(k_batched<double, OP_H>) : launch(k_batched<double, OP_D>);
-    return op == GBH_HIERARCHIZE ? launch(k_batched<float, OP_H>) : launch(k_batched<float, OP_D>);
+        return op == GBH_HIERARCHIZE ? launch(k_fused<double, OP_H>) : launch(k_fused<double, OP_D>);
+    return op == GBH_HIERARCHIZE ? launch(k_fused<float, OP_H>) : launch(k_fused<float, OP_D>);
 }
 
 int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
@@ -1029,13 +1440,6 @@ int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit)
     if (!plan || grid < -1 || grid >= plan->ngrids || spin_limit < 1) return GBH_EINVAL;
     plan->stall_grid = grid;
     plan->spin_limit = grid < 0 ? kSpinLimit : spin_limit;
-    if (grid < 0) {
-        // restore the real item counts
-        for (int o = 0; o < 2; ++o)
-            if (cudaMemcpy(plan->d_need[o], plan->need[o].data(), plan->need[o].size() * sizeof(int),
-                           cudaMemcpyHostToDevice) != cudaSuccess)
-                return GBH_ECUDA;
-    }
     return GBH_OK;
 }
 
@@ -1145,7 +1549,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
     // items in the plan's ticket order
     int nitems = 0;
     static int na_wave[kNoAllocMaxGrids], na_prev[kNoAllocMaxGrids];
-    const bool ok = order_items(g_na_host.info, n_grids, d, dtype, op, kNoAllocItemPoints, kWaveBytes,
+    const bool ok = order_items(g_na_host.info, n_grids, d, dtype, op, kNoAllocItemPoints, kWaveBytes, false,
                                 g_na_host.order, na_wave, na_prev, g_na_host.need, [&](const Item &it) {
                                     if (nitems >= cap) return false;
                                     g_na_host.items[nitems++] = it;
@@ -1172,6 +1576,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
         return GBH_ECUDA;
     BatchParams P{};
     P.spin_limit = kSpinLimit;
+    P.stall_grid = -1;
     P.items = reinterpret_cast<const Item *>(base + o_items);
     P.nitems = nitems;
     P.grids = reinterpret_cast<const GridInfo *>(base + o_info);
