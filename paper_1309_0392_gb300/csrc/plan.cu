@@ -163,7 +163,12 @@ constexpr int kPhases = 3 + 2 * kPlanMaxD;
 constexpr int kPhaseOut = kPhases - 1;
 constexpr int kGroupLevel = 12;                  // block level of long dimensions
 constexpr int kGroupElems = 8208;               // shared-memory elements per item
-constexpr int kSplitLevel = 13;                  // block level of dimensions longer than a tile (fused kernel)
+// fused kernel: tile size (elements), pole-set table size, CTAs per SM, and
+// the block level of dimensions longer than a tile
+constexpr int kFusedElems = 6144;
+constexpr int kFusedSets = 2048;
+constexpr int kFusedCtas = 3;
+constexpr int kSplitLevel = 12;
 
 template <int OP>
 __device__ __forceinline__ long long fx_op(long long v, long long L, long long R)
@@ -614,6 +619,26 @@ __device__ __forceinline__ void tile_long(V *sv, const TilePoles &tp, int poles,
     }
 }
 
+// Coarse-lattice poles of a split dimension (at most 2^5 + 1 points, a small
+// fraction of the grid): level by level through global memory, one thread
+// per pole, neighbouring threads on neighbouring poles.
+template <typename V, int OP>
+__device__ __forceinline__ void b_poles_loop(int L, V *base, int64_t S, FastDiv dS, int64_t n, int64_t st,
+                                             int64_t start, int64_t count)
+{
+    const int last = 1 << L;
+    for (int64_t t = start + threadIdx.x; t < start + count; t += blockDim.x) {
+        const int64_t o = fdiv(t, dS), j = t - o * S;
+        V *pp = base + o * S * n + j;
+        for (int step = 1; step <= L; ++step) {
+            const int lev = OP == OP_H ? L + 1 - step : step;
+            const int s = 1 << (L - lev);
+            for (int i = s; i < last; i += 2 * s)
+                __stcg(pp + i * st, any_op<OP>(__ldcg(pp + i * st), __ldcg(pp + (i - s) * st), __ldcg(pp + (i + s) * st)));
+        }
+    }
+}
+
 // One K_FUSED item: `count` pole sets of group q starting at pole set
 // `start` (block `blk` of a split dimension).
 template <typename ST, int OP>
@@ -621,6 +646,8 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
                                            int *s_em)
 {
     using V = typename std::conditional<sizeof(ST) == 8, long long, ST>::type;
+    // poles up to level kRegLevel are held in registers (one thread per pole)
+    constexpr int kRegLevel = sizeof(V) == 8 ? 4 : 5;
     V *sv = reinterpret_cast<V *>(sm);
     V *base = reinterpret_cast<V *>(sbase);
     const int tid = threadIdx.x;
@@ -637,7 +664,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
     const int cnt = Gc * M;
     const bool contig = Sa == 1 && !split;
     const unsigned magG = magic_u32(Gc), magM = magic_u32(M);
-    int64_t *pb = reinterpret_cast<int64_t *>(sm + (size_t)kGroupElems * sizeof(V));
+    int64_t *pb = reinterpret_cast<int64_t *>(sm + (size_t)kFusedElems * sizeof(V));
     if (!contig) {
         const int64_t boff = split ? ((int64_t)it.blk << m) * Sa : 0;
         for (int g = tid; g < Gc; g += blockDim.x) {
@@ -697,7 +724,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
         conv = true;
         // the conversion rides on the first sweep when that one keeps its
         // poles in registers
-        if (!fast || lfirst > 5) {
+        if (!fast || lfirst > kRegLevel) {
             for (int e = tid; e < cnt; e += blockDim.x) {
                 const double x = __longlong_as_double((long long)sv[e]);
                 sv[e] = (V)(fast ? b_to_fixed_fast(x, emax, c) : b_to_fixed_slow(x, emax, c));
@@ -720,7 +747,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
             tp.magA = magic_u32(tp.gfast ? Gc : tp.pps);
             tp.magK = magic_u32(tp.sk);
             const int poles = Gc * tp.pps;
-            if (lk <= 5) {
+            if (lk <= kRegLevel) {
                 if (conv) tile_regs_dispatch<V, OP, sizeof(ST) == 8>(lk, sv, tp, poles, emax, c);
                 else tile_regs_dispatch<V, OP, false>(lk, sv, tp, poles, emax, c);
             } else {
@@ -747,7 +774,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
 }
 
 template <typename ST, int OP>
-__global__ void __launch_bounds__(kBThreads, 2) k_fused(const BatchParams P)
+__global__ void __launch_bounds__(kBThreads, kFusedCtas) k_fused(const BatchParams P)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_item;
@@ -766,12 +793,9 @@ __global__ void __launch_bounds__(kBThreads, 2) k_fused(const BatchParams P)
             // coarse lattice of a split dimension: points a 2^m, stride 2^m S
             const int k = gi.grp_lo[it.dim], l = gi.l[k], m = gi.grp_m[it.dim];
             const int64_t n = ((int64_t)1 << l) + 1, S = gi.S[k];
-            const int L = l - m;    // at most 17 - kSplitLevel
+            const int L = l - m;    // at most 17 - kSplitLevel = 5
             const int64_t st = S << m;
-            if (L == 1) b_poles_regs<ST, 1, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
-            else if (L == 2) b_poles_regs<ST, 2, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
-            else if (L == 3) b_poles_regs<ST, 3, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
-            else if (L == 4) b_poles_regs<ST, 4, OP>(sbase, S, gi.divS[k], n, st, it.start, it.count);
+            b_poles_loop<ST, OP>(L, sbase, S, gi.divS[k], n, st, it.start, it.count);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -801,7 +825,7 @@ bool emit_fused_items(const GridInfo &gi, int op, int phase, int64_t chunk, Push
     const int64_t sets = gi.N / M;
     if (m < 0) {
         if (sub) return true;
-        const int64_t G = std::max<int64_t>(1, kGroupElems / M);
+        const int64_t G = std::min<int64_t>(kFusedSets, std::max<int64_t>(1, kFusedElems / M));
         for (int64_t t = 0; t < sets; t += G)
             if (!push(K_FUSED, q, t, std::min(G, sets - t), 0)) return false;
         return true;
@@ -815,7 +839,7 @@ bool emit_fused_items(const GridInfo &gi, int op, int phase, int64_t chunk, Push
             if (!push(K_LATT_NAT, q, t, std::min(ppi, sets - t), 0)) return false;
         return true;
     }
-    const int64_t G = std::max<int64_t>(1, kGroupElems / (((int64_t)1 << m) + 1));
+    const int64_t G = std::min<int64_t>(kFusedSets, std::max<int64_t>(1, kFusedElems / (((int64_t)1 << m) + 1)));
     for (int64_t a = 0; a < ((int64_t)1 << (l - m)); ++a)
         for (int64_t t = 0; t < sets; t += G)
             if (!push(K_FUSED, q, t, std::min(G, sets - t), (int)a)) return false;
@@ -952,8 +976,8 @@ double dgrowth(int lev)
 // kSplitLevel.  Fixed-point scales: hierarchization grows by at most 4 per
 // swept dimension (doubling form), the inverse by the largest sum of hat
 // weights along a pole per swept dimension.
-static_assert(((1 << kSplitLevel) + 1) <= kGroupElems, "a block must fit in a tile");
-static_assert(kGroupLevel + 5 - kSplitLevel <= 4, "the fused kernel's lattice poles have at most 4 levels");
+static_assert(((1 << kSplitLevel) + 1) <= kFusedElems, "a block must fit in a tile");
+static_assert(kGroupLevel + 5 - kSplitLevel <= 5, "the fused kernel's lattice poles have at most 5 levels");
 
 void make_groups(GridInfo &gi, int d)
 {
@@ -962,10 +986,10 @@ void make_groups(GridInfo &gi, int d)
     for (int k = 0; k < d;) {
         int hi = k, m = -1;
         int64_t M = ext(k);
-        if (M > kGroupElems) {
+        if (M > kFusedElems) {
             m = kSplitLevel;
         } else {
-            while (hi + 1 < d && M * ext(hi + 1) <= kGroupElems) {
+            while (hi + 1 < d && M * ext(hi + 1) <= kFusedElems) {
                 ++hi;
                 M *= ext(hi);
             }
@@ -1388,7 +1412,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.spin_limit = plan->spin_limit;
     P.stall_grid = plan->stall_grid;
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
-    const size_t smem = kGroupElems * es + kGroupElems * sizeof(int64_t) / 2;
+    const size_t smem = kFusedElems * es + kFusedSets * sizeof(int64_t);
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
