@@ -163,10 +163,9 @@ constexpr int kPhases = 3 + 2 * kPlanMaxD;
 constexpr int kPhaseOut = kPhases - 1;
 constexpr int kGroupLevel = 12;                  // block level of long dimensions
 constexpr int kGroupElems = 8208;               // shared-memory elements per item
-// fused kernel: tile size (elements), pole-set table size, CTAs per SM, and
-// the block level of dimensions longer than a tile
+// fused kernel: tile size (elements), CTAs per SM, and the block level of
+// dimensions longer than a tile
 constexpr int kFusedElems = 6144;
-constexpr int kFusedSets = 2048;
 constexpr int kFusedCtas = 3;
 constexpr int kSplitLevel = 12;
 
@@ -326,15 +325,16 @@ __device__ __forceinline__ void stream_elems(int64_t count, Src src, Dst dst)
     }
 }
 
-// Thread 0 takes the next ticket and waits (bounded) until the item's
-// dependency -- every item of the previous phase of its grid -- has finished.
+// Thread 0 takes the next ticket (or the one prefetched in `pref`) and waits
+// (bounded) until the item's dependency -- every item of the previous phase
+// of its grid -- has finished.
 // Returns the item index, or -1 when the queue is empty, the wait gave up
 // (status GBH_ETIMEOUT) or another CTA reported an error.  Every thread of
 // the CTA calls it.
-__device__ __forceinline__ int next_item(const BatchParams &P, int *s_item, int *s_abort)
+__device__ __forceinline__ int next_item(const BatchParams &P, int *s_item, int *s_abort, int *pref = nullptr)
 {
     if (threadIdx.x == 0) {
-        *s_item = (int)atomicAdd(P.ticket, 1u);
+        *s_item = (pref && *pref >= 0) ? *pref : (int)atomicAdd(P.ticket, 1u);
         *s_abort = 0;
         if (*s_item < P.nitems) {
             const Item it = P.items[*s_item];
@@ -354,6 +354,10 @@ __device__ __forceinline__ int next_item(const BatchParams &P, int *s_item, int 
                 }
             }
         }
+        // the following ticket, taken now so that its latency hides behind
+        // this item (tickets stay in order: a CTA holds at most one ticket
+        // beyond the one it works on, and dependencies point to smaller ones)
+        if (pref) *pref = (*s_item < P.nitems && !*s_abort) ? (int)atomicAdd(P.ticket, 1u) : -1;
     }
     __syncthreads();
     const int idx = *s_item;
@@ -570,15 +574,40 @@ __device__ __forceinline__ void tile_regs_dispatch(int L, V *sv, const TilePoles
 
 // Long poles: level by level in shared memory (hierarchize fine to coarse: a
 // point's two parents are coarser, hence still nodal; the inverse coarse to
-// fine); fixed point doubles the two ends of every pole too.  With enough
-// poles one warp takes a pole (warp-level barriers only), otherwise the whole
+// fine: a point's parents are final before it is computed); fixed point
+// doubles the two ends of every pole too.  Many poles: one thread per pole;
+// at least 4: a warp per pole (warp-level barriers only); fewer: the whole
 // CTA sweeps every pole level by level.
 template <typename V, int OP>
 __device__ __forceinline__ void tile_long(V *sv, const TilePoles &tp, int poles, int lk)
 {
     const int st = tp.sk * tp.sI, last = 1 << lk;
     constexpr bool kEnds = OP == OP_H && std::is_same<V, long long>::value;
-    if (poles >= 2 * (int)(blockDim.x >> 5)) {
+    if (poles >= 64) {
+        // many poles: one thread per pole, every level in order (neighbouring
+        // threads on neighbouring poles, so every access is conflict-free)
+        for (int p = threadIdx.x; p < poles; p += blockDim.x) {
+            V *q = sv + tp.base(p);
+            for (int step = 1; step <= lk; ++step) {
+                const int lev = OP == OP_H ? lk + 1 - step : step;
+                const int s = 1 << (lk - lev), s2 = 2 * s * st, ss = s * st;
+                V *r = q + ss;
+                V left = q[0];
+                for (int i = s; i < last; i += 2 * s, r += s2) {
+                    const V right = r[ss];
+                    const V v = any_op<OP>(r[0], left, right);
+                    r[0] = v;
+                    left = right;
+                }
+            }
+            if constexpr (kEnds) {
+                q[0] += q[0];
+                q[last * st] += q[last * st];
+            }
+        }
+        return;
+    }
+    if (poles >= 4) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int p = warp; p < poles; p += nw) {
             V *q = sv + tp.base(p);
@@ -664,30 +693,28 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
     const int cnt = Gc * M;
     const bool contig = Sa == 1 && !split;
     const unsigned magG = magic_u32(Gc), magM = magic_u32(M);
-    int64_t *pb = reinterpret_cast<int64_t *>(sm + (size_t)kFusedElems * sizeof(V));
-    if (!contig) {
-        const int64_t boff = split ? ((int64_t)it.blk << m) * Sa : 0;
-        for (int g = tid; g < Gc; g += blockDim.x) {
-            const int64_t t = it.start + g, o = fdiv(t, gi.divS[lo]);
-            pb[g] = o * Sout + (t - o * Sa) + boff;
-        }
-        __syncthreads();
+    // pole set t starts at (t / Sa) Sout + t % Sa (+ the block offset of a
+    // split dimension); a tile never crosses a multiple of Sa, so its pole
+    // sets are consecutive in memory (Sa > 1) or Sout apart (Sa = 1)
+    int64_t base0;
+    {
+        const int64_t o = fdiv(it.start, gi.divS[lo]);
+        base0 = o * Sout + (it.start - o * Sa) + (split ? ((int64_t)it.blk << m) * Sa : 0);
     }
-    const int64_t cbase = it.start * M;
     // global address of element w of the tile (its shared-memory slot is w)
     // and its index i within the pole set
     auto gaddr = [&](int w, int &i) -> int64_t {
         if (contig) {
             i = 0;
-            return cbase + w;
+            return base0 + w;
         }
         if (Sa == 1) {
             const int g = magM ? (int)__umulhi((unsigned)w, magM) : w;
             i = w - g * M;
-            return pb[g] + i;
+            return base0 + (int64_t)g * Sout + i;
         }
         i = magG ? (int)__umulhi((unsigned)w, magG) : w;
-        return pb[w - i * Gc] + (int64_t)i * Sa;
+        return base0 + (w - i * Gc) + (int64_t)i * Sa;
     };
     // every load of the tile in flight at once.  Other CTAs wrote this grid's
     // previous phase; the dependency wait (an acquire at gpu scope, then the
@@ -780,9 +807,10 @@ __global__ void __launch_bounds__(kBThreads, kFusedCtas) k_fused(const BatchPara
     __shared__ int s_item;
     __shared__ int s_abort;
     __shared__ int s_em;
+    int pref = -1;     // thread 0: prefetched ticket
     for (;;) {
         if (threadIdx.x == 0) s_em = 0;
-        const int idx = next_item(P, &s_item, &s_abort);
+        const int idx = next_item(P, &s_item, &s_abort, &pref);
         if (idx < 0) return;
         const Item it = P.items[idx];
         const GridInfo &gi = P.grids[it.grid];
@@ -823,12 +851,39 @@ bool emit_fused_items(const GridInfo &gi, int op, int phase, int64_t chunk, Push
     }
     if (pdims == 0) return true;
     const int64_t sets = gi.N / M;
+    // tiles of G pole sets that never cross a multiple of Sa (the stride of
+    // dimension lo), so that a tile's pole sets are evenly spaced in memory
+    const int64_t Sa = gi.S[lo];
+    auto tiles = [&](int64_t G, int blk) {
+        for (int64_t o = 0; o < sets; o += Sa)
+            for (int64_t t = o; t < o + Sa; t += G)
+                if (!push(K_FUSED, q, t, std::min(G, o + Sa - t), blk)) return false;
+        return true;
+    };
+    if (Sa == 1) {
+        // pole sets evenly spaced whatever the tile: no cut needed
+        auto rows = [&](int64_t G, int blk) {
+            for (int64_t t = 0; t < sets; t += G)
+                if (!push(K_FUSED, q, t, std::min(G, sets - t), blk)) return false;
+            return true;
+        };
+        if (m < 0) return sub ? true : rows(std::max<int64_t>(1, kFusedElems / M), 0);
+        const int l = gi.l[lo];
+        const bool blocks_now = (op == GBH_HIERARCHIZE) == (sub == 0);
+        if (!blocks_now) {
+            const int64_t ppi = std::max<int64_t>(kBThreads, chunk >> (l - m));
+            for (int64_t t = 0; t < sets; t += ppi)
+                if (!push(K_LATT_NAT, q, t, std::min(ppi, sets - t), 0)) return false;
+            return true;
+        }
+        const int64_t G = std::max<int64_t>(1, kFusedElems / (((int64_t)1 << m) + 1));
+        for (int64_t a = 0; a < ((int64_t)1 << (l - m)); ++a)
+            if (!rows(G, (int)a)) return false;
+        return true;
+    }
     if (m < 0) {
         if (sub) return true;
-        const int64_t G = std::min<int64_t>(kFusedSets, std::max<int64_t>(1, kFusedElems / M));
-        for (int64_t t = 0; t < sets; t += G)
-            if (!push(K_FUSED, q, t, std::min(G, sets - t), 0)) return false;
-        return true;
+        return tiles(std::max<int64_t>(1, kFusedElems / M), 0);
     }
     // split dimension: hierarchize blocks then lattice, the inverse the reverse
     const int l = gi.l[lo];
@@ -839,10 +894,9 @@ bool emit_fused_items(const GridInfo &gi, int op, int phase, int64_t chunk, Push
             if (!push(K_LATT_NAT, q, t, std::min(ppi, sets - t), 0)) return false;
         return true;
     }
-    const int64_t G = std::min<int64_t>(kFusedSets, std::max<int64_t>(1, kFusedElems / (((int64_t)1 << m) + 1)));
+    const int64_t G = std::max<int64_t>(1, kFusedElems / (((int64_t)1 << m) + 1));
     for (int64_t a = 0; a < ((int64_t)1 << (l - m)); ++a)
-        for (int64_t t = 0; t < sets; t += G)
-            if (!push(K_FUSED, q, t, std::min(G, sets - t), (int)a)) return false;
+        if (!tiles(G, (int)a)) return false;
     return true;
 }
 
@@ -1412,7 +1466,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.spin_limit = plan->spin_limit;
     P.stall_grid = plan->stall_grid;
     const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
-    const size_t smem = kFusedElems * es + kFusedSets * sizeof(int64_t);
+    const size_t smem = kFusedElems * es;
     auto launch = [&](auto kern) -> int {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
