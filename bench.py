@@ -470,7 +470,8 @@ def run_ours(args):
 
 def run_case(args):
     """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith]]`
-    (path auto/plain/fused, arith 0/1/2) or `scheme:d,n:op:dtype` (op h/d/a,
+    (path auto/plain/fused, arith 0/1/2), `scheme:d,n:op:dtype` or
+    `gather:d,n:op:dtype` (the scheme's gather into the sparse grid) (op h/d/a,
     dtype f64/f32), run warmup + steps times; prints one JSON line with the
     median time and the per-kernel launch times of a second, profiled pass."""
     import torch
@@ -497,6 +498,9 @@ def run_case(args):
         plan.bind(grids)
         fn = lambda: plan.execute(opc)  # noqa: E731
         pts = plan.total_points
+        if kind == "gather":
+            sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
+            fn = lambda: plan.gather(sparse)  # noqa: E731
     for _ in range(args.warmup):
         fn()
     ms = _ms(fn, max(1, args.steps))

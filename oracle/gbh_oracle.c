@@ -456,7 +456,8 @@ void orc_sparse_index_of_grid(int d, int n, const int *levels, int64_t *out)
 /* Gather (Sec. 2, "Hierarchization as preprocessing"): sparse = sum over the
  * grids of coeff_g * alpha_g, where a point absent from a grid contributes 0.
  * Grids are added in the order given (scheme enumeration order), starting
- * from 0, each as sparse[p] = sparse[p] + c * alpha. */
+ * from 0, each term as one fused multiply-add, sparse[p] = fma(c, alpha,
+ * sparse[p]) (one rounding per term; the paper fixes no rounding order). */
 void orc_gather(int d, int n, int ngrids, const int *levels, const double *coeffs,
                 const double *const *grids, double *sparse)
 {
@@ -467,7 +468,7 @@ void orc_gather(int d, int n, int ngrids, const int *levels, const double *coeff
         const int64_t N = orc_num_points(d, l);
         int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * N);
         orc_sparse_index_of_grid(d, n, l, idx);
-        for (int64_t f = 0; f < N; ++f) sparse[idx[f]] = sparse[idx[f]] + coeffs[g] * grids[g][f];
+        for (int64_t f = 0; f < N; ++f) sparse[idx[f]] = fma(coeffs[g], grids[g][f], sparse[idx[f]]);
         free(idx);
     }
 }

@@ -955,54 +955,101 @@ bool emit_items(const GridInfo &gi, int d, int dtype, int op, int phase, int64_t
 
 struct GatherParams {
     int d;
-    int nsub;
     const int64_t *sub_off;     // [nsub + 1] first sparse point of every subspace
     const int *sub_j;           // [nsub * d] subspace levels
     const int *list_off;        // [nsub + 1]
     const int *list;            // grids containing each subspace, enumeration order
+    const int2 *chunks;         // (subspace, first point in it) of every CTA's chunk
+    int nchunks;
     const GridInfo *grids;
     void *const *ptrs;
     const double *coeffs;
     double *sparse;
-    int64_t total;
     int fp64;
 };
 
-__global__ void __launch_bounds__(256) k_gather(const GatherParams P)
+constexpr int kGatherPer = 4;                      // points per thread
+constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
+
+// A CTA takes a chunk of one subspace block (positions p, dimension 0
+// fastest) and runs through the grids containing the subspace in enumeration
+// order, 256 at a time: for grid g its point of position (p_k) sits at
+// B_g + sum_k p_k T_gk, with B_g = sum_{j_k >= 1} S_k 2^{l_k - j_k} and
+// T_gk = S_k 2^{l_k - j_k + 1} (j_k >= 1) or S_k 2^{l_k} (j_k = 0, the two
+// boundary points).  Every term is one fused multiply-add, in grid order.
+__global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
 {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.total;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = P.nsub - 1;          // last subspace with sub_off <= p
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.sub_off[mid] <= p) lo = mid;
-            else hi = mid - 1;
+    __shared__ int64_t sB[256];
+    __shared__ int64_t sT[256][kPlanMaxD];
+    __shared__ double sC[256];
+    __shared__ const void *sP[256];
+    __shared__ int sj[kPlanMaxD], sbits[kPlanMaxD];
+    const int d = P.d, tid = threadIdx.x;
+    for (int c = blockIdx.x; c < P.nchunks; c += gridDim.x) {
+        const int2 ch = P.chunks[c];
+        const int sb = ch.x;
+        const int64_t size = P.sub_off[sb + 1] - P.sub_off[sb];
+        if (tid < d) {
+            const int j = P.sub_j[sb * d + tid];
+            sj[tid] = j;
+            sbits[tid] = j == 0 ? 1 : j - 1;   // bits of the position along dimension tid
         }
-        const int sb = lo;
-        int64_t pos = p - P.sub_off[sb];
-        int j[kPlanMaxD];
-        int64_t ps[kPlanMaxD];
-        for (int k = 0; k < P.d; ++k) {
-            j[k] = P.sub_j[sb * P.d + k];
-            const int64_t w = j[k] == 0 ? 2 : ((int64_t)1 << (j[k] - 1));
-            ps[k] = pos % w;
-            pos /= w;
-        }
-        double acc = 0.0;
-        for (int q = P.list_off[sb]; q < P.list_off[sb + 1]; ++q) {
-            const int g = P.list[q];
-            const GridInfo &gi = P.grids[g];
-            int64_t f = 0;
-            for (int k = 0; k < P.d; ++k) {
-                const int l = gi.l[k];
-                const int64_t i = j[k] == 0 ? ps[k] << l : (2 * ps[k] + 1) << (l - j[k]);
-                f += i * gi.S[k];
+        __syncthreads();
+        int npts = 0;
+#pragma unroll
+        for (int r = 0; r < kGatherPer; ++r)
+            if ((int64_t)ch.y + tid + r * 256 < size) npts = r + 1;
+        double acc[kGatherPer];
+#pragma unroll
+        for (int r = 0; r < kGatherPer; ++r) acc[r] = 0.0;
+        const int q0 = P.list_off[sb], q1 = P.list_off[sb + 1];
+        for (int qb = q0; qb < q1; qb += 256) {
+            const int nb = q1 - qb < 256 ? q1 - qb : 256;
+            if (tid < nb) {
+                const int g = P.list[qb + tid];
+                const GridInfo &gi = P.grids[g];
+                int64_t B = 0;
+                for (int k = 0; k < kPlanMaxD; ++k) {
+                    int64_t T = 0;
+                    if (k < d) {
+                        const int l = gi.l[k], j = sj[k];
+                        T = j == 0 ? gi.S[k] << l : gi.S[k] << (l - j + 1);
+                        if (j > 0) B += gi.S[k] << (l - j);
+                    }
+                    sT[tid][k] = T;
+                }
+                sB[tid] = B;
+                sC[tid] = P.coeffs[g];
+                sP[tid] = P.ptrs[g];
             }
-            const double a = P.fp64 ? __ldg(reinterpret_cast<const double *>(P.ptrs[g]) + f)
-                                    : (double)__ldg(reinterpret_cast<const float *>(P.ptrs[g]) + f);
-            acc = __dadd_rn(acc, __dmul_rn(P.coeffs[g], a));
+            __syncthreads();
+            for (int b = 0; b < nb; ++b) {
+                const double cg = sC[b];
+                double a[kGatherPer];
+#pragma unroll
+                for (int r = 0; r < kGatherPer; ++r) {
+                    a[r] = 0.0;
+                    if (r < npts) {
+                        int64_t f = sB[b], rest = (int64_t)ch.y + tid + r * 256;
+#pragma unroll
+                        for (int k = 0; k < kPlanMaxD; ++k)
+                            if (k < d) {
+                                f += (rest & ((1ll << sbits[k]) - 1)) * sT[b][k];
+                                rest >>= sbits[k];
+                            }
+                        a[r] = P.fp64 ? __ldg(reinterpret_cast<const double *>(sP[b]) + f)
+                                      : (double)__ldg(reinterpret_cast<const float *>(sP[b]) + f);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kGatherPer; ++r) acc[r] = __fma_rn(cg, a[r], acc[r]);
+            }
+            __syncthreads();
         }
-        P.sparse[p] = acc;
+        double *out = P.sparse + P.sub_off[sb] + ch.y;
+#pragma unroll
+        for (int r = 0; r < kGatherPer; ++r)
+            if (r < npts) out[tid + r * 256] = acc[r];
     }
 }
 
@@ -1089,7 +1136,8 @@ struct gbh_plan {
     size_t scratch_bytes = 0;
     int64_t *d_sub_off = nullptr;
     int *d_sub_j = nullptr, *d_list_off = nullptr, *d_list = nullptr;
-    int nsub = 0;
+    int2 *d_chunks = nullptr;
+    int nsub = 0, nchunks = 0;
     void **h_ptrs = nullptr;          // pinned staging for bind
     bool bound = false;
     int dev = 0;
@@ -1114,6 +1162,7 @@ void free_plan(gbh_plan *p)
     cudaFree(p->d_sub_j);
     cudaFree(p->d_list_off);
     cudaFree(p->d_list);
+    cudaFree(p->d_chunks);
     if (p->h_ptrs) cudaFreeHost(p->h_ptrs);
     delete p;
 }
@@ -1280,6 +1329,14 @@ int build_sparse(gbh_plan *p)
     loff.push_back((int)list.size());
     p->nsub = (int)js.size() / d;
     p->sparse_points = acc;
+    std::vector<int2> chunks;
+    for (int sb = 0; sb < p->nsub; ++sb)
+        for (int64_t q = 0; q < off[sb + 1] - off[sb]; q += kGatherChunk) {
+            if (q > INT32_MAX) return GBH_ERANGE;
+            chunks.push_back(make_int2(sb, (int)q));
+        }
+    p->nchunks = (int)chunks.size();
+    if (int e = upload(&p->d_chunks, chunks)) return e;
     if (int e = upload(&p->d_sub_off, off)) return e;
     if (int e = upload(&p->d_sub_j, js)) return e;
     if (int e = upload(&p->d_list_off, loff)) return e;
@@ -1493,20 +1550,19 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     GatherParams G{};
     G.d = plan->d;
-    G.nsub = plan->nsub;
     G.sub_off = plan->d_sub_off;
     G.sub_j = plan->d_sub_j;
     G.list_off = plan->d_list_off;
     G.list = plan->d_list;
+    G.chunks = plan->d_chunks;
+    G.nchunks = plan->nchunks;
     G.grids = plan->d_info;
     G.ptrs = plan->d_ptrs;
     G.coeffs = plan->d_coeffs;
     G.sparse = sparse;
-    G.total = plan->sparse_points;
     G.fp64 = plan->dtype == GBH_F64;
-    const int64_t want = (G.total + 255) / 256;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
-    ProfScope ps("gather", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * G.total);
+    const int grid = std::max(1, std::min(G.nchunks, num_sms() * 4));
+    ProfScope ps("gather", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * plan->sparse_points);
     k_gather<<<grid, 256, 0, s>>>(G);
     ps.done();
     count_launches(1);
