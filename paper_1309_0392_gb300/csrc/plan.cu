@@ -968,15 +968,18 @@ struct GatherParams {
     int fp64;
 };
 
-constexpr int kGatherPer = 4;                      // points per thread
+constexpr int kGatherPer = 2;                      // points per thread
 constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
+constexpr int kGatherAhead = 4;                    // grids whose loads are in flight together
 
 // A CTA takes a chunk of one subspace block (positions p, dimension 0
 // fastest) and runs through the grids containing the subspace in enumeration
 // order, 256 at a time: for grid g its point of position (p_k) sits at
 // B_g + sum_k p_k T_gk, with B_g = sum_{j_k >= 1} S_k 2^{l_k - j_k} and
 // T_gk = S_k 2^{l_k - j_k + 1} (j_k >= 1) or S_k 2^{l_k} (j_k = 0, the two
-// boundary points).  Every term is one fused multiply-add, in grid order.
+// boundary points).  Every term is one fused multiply-add, in grid order;
+// the loads of the next kGatherAhead grids are in flight while the current
+// ones are summed.
 __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
 {
     __shared__ int64_t sB[256];
@@ -1002,6 +1005,18 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
         double acc[kGatherPer];
 #pragma unroll
         for (int r = 0; r < kGatherPer; ++r) acc[r] = 0.0;
+        // value of this thread's point r in batch grid b (0 if absent)
+        auto fetch = [&](int b, int r) -> double {
+            int64_t f = sB[b], rest = (int64_t)ch.y + tid + r * 256;
+#pragma unroll
+            for (int k = 0; k < kPlanMaxD; ++k)
+                if (k < d) {
+                    f += (rest & ((1ll << sbits[k]) - 1)) * sT[b][k];
+                    rest >>= sbits[k];
+                }
+            return P.fp64 ? __ldg(reinterpret_cast<const double *>(sP[b]) + f)
+                          : (double)__ldg(reinterpret_cast<const float *>(sP[b]) + f);
+        };
         const int q0 = P.list_off[sb], q1 = P.list_off[sb + 1];
         for (int qb = q0; qb < q1; qb += 256) {
             const int nb = q1 - qb < 256 ? q1 - qb : 256;
@@ -1023,26 +1038,31 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
                 sP[tid] = P.ptrs[g];
             }
             __syncthreads();
-            for (int b = 0; b < nb; ++b) {
-                const double cg = sC[b];
-                double a[kGatherPer];
+            double cur[kGatherAhead][kGatherPer];
 #pragma unroll
-                for (int r = 0; r < kGatherPer; ++r) {
-                    a[r] = 0.0;
-                    if (r < npts) {
-                        int64_t f = sB[b], rest = (int64_t)ch.y + tid + r * 256;
+            for (int a = 0; a < kGatherAhead; ++a)
 #pragma unroll
-                        for (int k = 0; k < kPlanMaxD; ++k)
-                            if (k < d) {
-                                f += (rest & ((1ll << sbits[k]) - 1)) * sT[b][k];
-                                rest >>= sbits[k];
-                            }
-                        a[r] = P.fp64 ? __ldg(reinterpret_cast<const double *>(sP[b]) + f)
-                                      : (double)__ldg(reinterpret_cast<const float *>(sP[b]) + f);
+                for (int r = 0; r < kGatherPer; ++r) cur[a][r] = (a < nb && r < npts) ? fetch(a, r) : 0.0;
+            for (int b0 = 0; b0 < nb; b0 += kGatherAhead) {
+                double nxt[kGatherAhead][kGatherPer];
+#pragma unroll
+                for (int a = 0; a < kGatherAhead; ++a) {
+                    const int b = b0 + kGatherAhead + a;
+#pragma unroll
+                    for (int r = 0; r < kGatherPer; ++r) nxt[a][r] = (b < nb && r < npts) ? fetch(b, r) : 0.0;
+                }
+#pragma unroll
+                for (int a = 0; a < kGatherAhead; ++a) {
+                    if (b0 + a < nb) {
+                        const double cg = sC[b0 + a];
+#pragma unroll
+                        for (int r = 0; r < kGatherPer; ++r) acc[r] = __fma_rn(cg, cur[a][r], acc[r]);
                     }
                 }
 #pragma unroll
-                for (int r = 0; r < kGatherPer; ++r) acc[r] = __fma_rn(cg, a[r], acc[r]);
+                for (int a = 0; a < kGatherAhead; ++a)
+#pragma unroll
+                    for (int r = 0; r < kGatherPer; ++r) cur[a][r] = nxt[a][r];
             }
             __syncthreads();
         }
