@@ -1038,31 +1038,34 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
                 sP[tid] = P.ptrs[g];
             }
             __syncthreads();
-            double cur[kGatherAhead][kGatherPer];
-#pragma unroll
-            for (int a = 0; a < kGatherAhead; ++a)
-#pragma unroll
-                for (int r = 0; r < kGatherPer; ++r) cur[a][r] = (a < nb && r < npts) ? fetch(a, r) : 0.0;
-            for (int b0 = 0; b0 < nb; b0 += kGatherAhead) {
-                double nxt[kGatherAhead][kGatherPer];
-#pragma unroll
-                for (int a = 0; a < kGatherAhead; ++a) {
-                    const int b = b0 + kGatherAhead + a;
-#pragma unroll
-                    for (int r = 0; r < kGatherPer; ++r) nxt[a][r] = (b < nb && r < npts) ? fetch(b, r) : 0.0;
-                }
-#pragma unroll
-                for (int a = 0; a < kGatherAhead; ++a) {
-                    if (b0 + a < nb) {
-                        const double cg = sC[b0 + a];
-#pragma unroll
-                        for (int r = 0; r < kGatherPer; ++r) acc[r] = __fma_rn(cg, cur[a][r], acc[r]);
-                    }
-                }
+            if (npts > 0) {
+                double cur[kGatherAhead][kGatherPer];
 #pragma unroll
                 for (int a = 0; a < kGatherAhead; ++a)
 #pragma unroll
-                    for (int r = 0; r < kGatherPer; ++r) cur[a][r] = nxt[a][r];
+                    for (int r = 0; r < kGatherPer; ++r) cur[a][r] = (a < nb && r < npts) ? fetch(a, r) : 0.0;
+                for (int b0 = 0; b0 < nb; b0 += kGatherAhead) {
+                    double nxt[kGatherAhead][kGatherPer];
+#pragma unroll
+                    for (int a = 0; a < kGatherAhead; ++a) {
+                        const int b = b0 + kGatherAhead + a;
+#pragma unroll
+                        for (int r = 0; r < kGatherPer; ++r) nxt[a][r] = (b < nb && r < npts) ? fetch(b, r) : 0.0;
+                    }
+#pragma unroll
+                    for (int a = 0; a < kGatherAhead; ++a) {
+                        if (b0 + a < nb) {
+                            const double cg = sC[b0 + a];
+#pragma unroll
+                            for (int r = 0; r < kGatherPer; ++r)
+                                if (r < npts) acc[r] = __fma_rn(cg, cur[a][r], acc[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int a = 0; a < kGatherAhead; ++a)
+#pragma unroll
+                        for (int r = 0; r < kGatherPer; ++r) cur[a][r] = nxt[a][r];
+                }
             }
             __syncthreads();
         }
