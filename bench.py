@@ -470,7 +470,7 @@ def run_ours(args):
 
 def run_case(args):
     """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith]]`
-    (path auto/plain/fused, arith 0/1/2), `scheme:d,n:op:dtype` or
+    (path auto/plain/fused/grouped, arith 0/1/2), `scheme:d,n:op:dtype` or
     `gather:d,n:op:dtype` (the scheme's gather into the sparse grid) (op h/d/a,
     dtype f64/f32), run warmup + steps times; prints one JSON line with the
     median time and the per-kernel launch times of a second, profiled pass."""
@@ -479,8 +479,8 @@ def run_case(args):
     import paper_1309_0392_gb300 as gbh
     from paper_1309_0392_gb300 import _lib
     kind, spec, op, dt, *extra = args.case.split(":")
-    path = {"auto": gbh.GBH_PATH_AUTO, "plain": gbh.GBH_PATH_PLAIN,
-            "fused": gbh.GBH_PATH_FUSED}[extra[0] if extra else "auto"]
+    path = {"auto": gbh.GBH_PATH_AUTO, "plain": gbh.GBH_PATH_PLAIN, "fused": gbh.GBH_PATH_FUSED,
+            "grouped": gbh.GBH_PATH_GROUPED}[extra[0] if extra else "auto"]
     arith = int(extra[1]) if len(extra) > 1 else 0
     dtype = torch.float64 if dt == "f64" else torch.float32
     opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}[op]

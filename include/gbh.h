@@ -97,7 +97,11 @@ typedef enum {
     GBH_PATH_AUTO = 0,   /* planner's choice (fused when available)             */
     GBH_PATH_PLAIN = 1,  /* one sweep kernel per dimension (native arithmetic
                             unless arith = 2)                                   */
-    GBH_PATH_FUSED = 2   /* dyadic-tile kernels, all dimensions per tile        */
+    GBH_PATH_FUSED = 2,  /* dyadic-tile kernels, all dimensions per tile        */
+    GBH_PATH_GROUPED = 3 /* one pass per group of consecutive dimensions whose
+                            pole sets fit in a shared-memory tile (hierarchize
+                            and dehierarchize; GBH_EUNSUPPORTED for a level of
+                            13 or more, d > 8 or the transpose)                 */
 } gbh_path;
 
 /* Options of gbh_transform.  Zero-initialise, then set what is wanted. */

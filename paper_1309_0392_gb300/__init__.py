@@ -12,7 +12,7 @@ import ctypes
 
 from . import _lib
 from ._lib import (GBH_ADJOINT, GBH_DEHIERARCHIZE, GBH_HIERARCHIZE, GBH_PATH_AUTO,  # noqa: F401
-                   GBH_PATH_FUSED, GBH_PATH_PLAIN, GBH_ARITH_AUTO, GBH_ARITH_NATIVE,
+                   GBH_PATH_FUSED, GBH_PATH_GROUPED, GBH_PATH_PLAIN, GBH_ARITH_AUTO, GBH_ARITH_NATIVE,
                    GBH_ARITH_FIXED, GbhError)
 
 __all__ = ["hierarchize", "dehierarchize", "hierarchize_adjoint", "transform", "num_points",

@@ -17,7 +17,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "gbh.h")
 
 GBH_F32, GBH_F64 = 0, 1
 GBH_HIERARCHIZE, GBH_DEHIERARCHIZE, GBH_ADJOINT = 0, 1, 2
-GBH_PATH_AUTO, GBH_PATH_PLAIN, GBH_PATH_FUSED = 0, 1, 2
+GBH_PATH_AUTO, GBH_PATH_PLAIN, GBH_PATH_FUSED, GBH_PATH_GROUPED = 0, 1, 2, 3
 GBH_ARITH_AUTO, GBH_ARITH_NATIVE, GBH_ARITH_FIXED = 0, 1, 2
 
 STATUS = {0: "GBH_OK", -1: "GBH_EINVAL", -2: "GBH_EDTYPE", -3: "GBH_EALIGN", -4: "GBH_ERANGE",

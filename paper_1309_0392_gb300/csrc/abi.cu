@@ -163,13 +163,15 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     g.batch = batch;
     g.total = g.N * batch;
     const int path = opt ? opt->path : GBH_PATH_AUTO;
-    if (path != GBH_PATH_AUTO && path != GBH_PATH_PLAIN && path != GBH_PATH_FUSED) return GBH_EINVAL;
+    if (path != GBH_PATH_AUTO && path != GBH_PATH_PLAIN && path != GBH_PATH_FUSED && path != GBH_PATH_GROUPED)
+        return GBH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (path == GBH_PATH_PLAIN) return plain_transform(data, g, dtype, op, s, opt && opt->arith == 2);
     if (path == GBH_PATH_FUSED) {
         if (!fused_supported(g, dtype, op)) return GBH_EUNSUPPORTED;
         return fused_transform(data, g, dtype, op, opt, s);
     }
+    if (path == GBH_PATH_GROUPED) return grouped_transform(data, g, dtype, op, s);
     // planner's choice: the fused path when it takes the shape and the grid is
     // large enough to tile, else one sweep per dimension
     if (g.N >= 4096 && fused_preferred(g, dtype, op)) return fused_transform(data, g, dtype, op, opt, s);

@@ -575,53 +575,42 @@ __device__ __forceinline__ void tile_regs_dispatch(int L, V *sv, const TilePoles
 // Long poles: level by level in shared memory (hierarchize fine to coarse: a
 // point's two parents are coarser, hence still nodal; the inverse coarse to
 // fine: a point's parents are final before it is computed); fixed point
-// doubles the two ends of every pole too.  Many poles: one thread per pole;
-// at least 4: a warp per pole (warp-level barriers only); fewer: the whole
-// CTA sweeps every pole level by level.
+// doubles the two ends of every pole too.  At least 4 poles: a group of
+// lanes of one warp per pole (one lane when there are many poles, the whole
+// warp when there are few; warp-level barriers only); fewer: the whole CTA
+// sweeps every pole level by level.
 template <typename V, int OP>
 __device__ __forceinline__ void tile_long(V *sv, const TilePoles &tp, int poles, int lk)
 {
     const int st = tp.sk * tp.sI, last = 1 << lk;
     constexpr bool kEnds = OP == OP_H && std::is_same<V, long long>::value;
-    if (poles >= 64) {
-        // many poles: one thread per pole, every level in order (neighbouring
-        // threads on neighbouring poles, so every access is conflict-free)
-        for (int p = threadIdx.x; p < poles; p += blockDim.x) {
-            V *q = sv + tp.base(p);
-            for (int step = 1; step <= lk; ++step) {
-                const int lev = OP == OP_H ? lk + 1 - step : step;
-                const int s = 1 << (lk - lev), s2 = 2 * s * st, ss = s * st;
-                V *r = q + ss;
-                V left = q[0];
-                for (int i = s; i < last; i += 2 * s, r += s2) {
-                    const V right = r[ss];
-                    const V v = any_op<OP>(r[0], left, right);
-                    r[0] = v;
-                    left = right;
-                }
-            }
-            if constexpr (kEnds) {
-                q[0] += q[0];
-                q[last * st] += q[last * st];
-            }
-        }
-        return;
-    }
+    const int nw = blockDim.x >> 5;
     if (poles >= 4) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int p = warp; p < poles; p += nw) {
-            V *q = sv + tp.base(p);
+        // lpp lanes of one warp per pole (a power of two, as many as the
+        // poles leave room for): the lanes split each level, warp barriers
+        // between levels; every lane of a warp runs every level
+        int lpp = 1;
+        while (lpp < 32 && 2 * lpp * poles <= (int)blockDim.x) lpp *= 2;
+        const int lane = threadIdx.x & 31, sub = lane & (lpp - 1);
+        const int per_warp = 32 / lpp;
+        for (int p0 = (threadIdx.x >> 5) * per_warp; p0 < poles; p0 += nw * per_warp) {
+            const int p = p0 + lane / lpp;
+            const bool on = p < poles;
+            V *q = sv + (on ? tp.base(p) : 0);
             for (int step = 1; step <= lk; ++step) {
                 const int lev = OP == OP_H ? lk + 1 - step : step;
                 const int s = 1 << (lk - lev), per = 1 << (lev - 1);
-                for (int j = lane; j < per; j += 32) {
-                    const int i = (2 * j + 1) * s;
-                    q[i * st] = any_op<OP>(q[i * st], q[(i - s) * st], q[(i + s) * st]);
+                if (on) {
+                    for (int j = sub; j < per; j += lpp) {
+                        const int i = (2 * j + 1) * s;
+                        q[i * st] = any_op<OP>(q[i * st], q[(i - s) * st], q[(i + s) * st]);
+                    }
                 }
                 __syncwarp();
             }
             if constexpr (kEnds) {
-                if (lane < 2) q[lane * last * st] += q[lane * last * st];
+                if (on)
+                    for (int e = sub; e < 2; e += lpp) q[e * last * st] += q[e * last * st];
                 __syncwarp();
             }
         }
@@ -833,6 +822,45 @@ __global__ void __launch_bounds__(kBThreads, kFusedCtas) k_fused(const BatchPara
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// single grids by dimension groups (non-persistent)
+// ---------------------------------------------------------------------------
+//
+// A single grid (or a same-shape batch) transformed group by group: one
+// launch per group of dimensions, one CTA per tile, the batched kernel's
+// item body.  The default path takes it when grouping crosses memory fewer
+// times than one sweep per dimension (e.g. (6,6,5,5,5): dimensions {0,1},
+// {2,3}, {4}).  Tiles never cross a multiple of Sa (the stride of the group's
+// first dimension).
+struct GroupLaunch {
+    GridInfo gi;
+    int q;
+    int64_t Sa, G, tiles_per_o, sets;
+};
+
+template <typename ST, int OP>
+__global__ void __launch_bounds__(kBThreads, kFusedCtas) k_grouped(const __grid_constant__ GroupLaunch L, ST *u)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_em;
+    if (threadIdx.x == 0) s_em = 0;
+    __syncthreads();
+    Item it{};
+    const int64_t b = blockIdx.x;
+    if (L.Sa == 1) {
+        it.start = b * L.G;
+        it.count = L.sets - it.start < L.G ? L.sets - it.start : L.G;
+    } else {
+        const int64_t o = b / L.tiles_per_o;
+        it.start = o * L.Sa + (b - o * L.tiles_per_o) * L.G;
+        const int64_t end = (o + 1) * L.Sa;
+        it.count = end - it.start < L.G ? end - it.start : L.G;
+    }
+    it.dim = L.q;
+    it.kind = K_FUSED;
+    fused_item<ST, OP>(it, L.gi, u + (int64_t)blockIdx.y * L.gi.N, sm, &s_em);
+}
 
 // Items of the fused kernel for one grid and phase: group q runs in phases
 // 2 + 2q (+1 for the second part of a split dimension).
@@ -1136,7 +1164,86 @@ void make_groups(GridInfo &gi, int d)
     gi.ngroups = q;
 }
 
+template <typename ST, int OP>
+int run_grouped(const GridInfo &gi, int64_t batch, ST *u, cudaStream_t st)
+{
+    const size_t smem = kFusedElems * sizeof(ST);
+    cudaFuncSetAttribute(k_grouped<ST, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int q = 0; q < gi.ngroups; ++q) {
+        GroupLaunch L{};
+        L.gi = gi;
+        L.q = q;
+        int64_t M = 1;
+        int pdims = 0;
+        for (int k = gi.grp_lo[q]; k <= gi.grp_hi[q]; ++k) {
+            M *= ((int64_t)1 << gi.l[k]) + 1;
+            pdims += gi.l[k] > 0;
+        }
+        if (pdims == 0) continue;
+        L.Sa = gi.S[gi.grp_lo[q]];
+        L.sets = gi.N / M;
+        L.G = std::max<int64_t>(1, kFusedElems / M);
+        int64_t tiles;
+        if (L.Sa == 1) {
+            tiles = (L.sets + L.G - 1) / L.G;
+        } else {
+            L.tiles_per_o = (L.Sa + L.G - 1) / L.G;
+            tiles = (L.sets / L.Sa) * L.tiles_per_o;
+        }
+        if (tiles > INT32_MAX || batch > 65535) return GBH_ERANGE;
+        ProfScope ps("grouped", st, 2.0 * sizeof(ST) * (double)gi.N * batch);
+        k_grouped<ST, OP><<<dim3((unsigned)tiles, (unsigned)batch), kBThreads, smem, st>>>(L, u);
+        ps.done();
+        count_launches(1);
+        if (int e = check_launch()) return e;
+    }
+    return GBH_OK;
+}
+
+bool make_grid_info(const Geom &g, GridInfo *gi)
+{
+    if (g.d > kPlanMaxD) return false;
+    std::memset(gi, 0, sizeof(*gi));
+    for (int k = 0; k < g.d; ++k) {
+        gi->l[k] = g.l[k];
+        gi->S[k] = g.S[k];
+        gi->divS[k] = make_fastdiv(g.S[k]);
+    }
+    gi->N = g.N;
+    make_groups(*gi, g.d);
+    for (int q = 0; q < gi->ngroups; ++q)
+        if (gi->grp_m[q] >= 0) return false;          // a dimension longer than a tile
+    return true;
+}
+
 }  // namespace
+
+int grouped_passes(const Geom &g)
+{
+    GridInfo gi;
+    if (!make_grid_info(g, &gi)) return -1;
+    int passes = 0;
+    for (int q = 0; q < gi.ngroups; ++q) {
+        bool any = false;
+        for (int k = gi.grp_lo[q]; k <= gi.grp_hi[q]; ++k) any |= gi.l[k] > 0;
+        passes += any;
+    }
+    return passes;
+}
+
+int grouped_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s)
+{
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return GBH_EUNSUPPORTED;
+    GridInfo gi;
+    if (!make_grid_info(g, &gi)) return GBH_EUNSUPPORTED;
+    if (dtype == GBH_F64) {
+        double *u = static_cast<double *>(data);
+        return op == GBH_HIERARCHIZE ? run_grouped<double, OP_H>(gi, g.batch, u, s) : run_grouped<double, OP_D>(gi, g.batch, u, s);
+    }
+    float *u = static_cast<float *>(data);
+    return op == GBH_HIERARCHIZE ? run_grouped<float, OP_H>(gi, g.batch, u, s) : run_grouped<float, OP_D>(gi, g.batch, u, s);
+}
+
 }  // namespace gbh
 
 using namespace gbh;

@@ -96,6 +96,27 @@ def test_plain_fixed_point_fp64(levels, op):
     assert rel_err(run(u, levels, op, path=gbh.GBH_PATH_PLAIN, arith=2), ORACLE[op](u, levels), u) <= TOL64
 
 
+@pytest.mark.parametrize("levels", [l for l in LEVELS if len(l) >= 2 and max(l) <= 12]
+                         + [(6, 6, 5, 5, 5), (3, 3, 3, 3, 3, 3, 2, 2), (12, 3), (2, 2, 11)])
+@pytest.mark.parametrize("op", ["h", "d"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_grouped_path(levels, op, dtype):
+    """One pass per group of consecutive dimensions (shared-memory tiles of
+    pole sets, per-tile fixed point in fp64)."""
+    tol = TOL64 if dtype == torch.float64 else TOL32
+    u = inputs.uniform(levels, 400 + len(levels), dtype=np.float64 if dtype == torch.float64 else np.float32)
+    got = run(u, levels, op, dtype=dtype, path=gbh.GBH_PATH_GROUPED)
+    ud = u.astype(np.float64)
+    assert rel_err(got, ORACLE[op](ud, levels), ud) <= tol
+
+
+def test_grouped_path_declines():
+    for levels, op in [((13, 2), gbh.GBH_HIERARCHIZE), ((4, 4), gbh.GBH_ADJOINT), ((1,) * 9, gbh.GBH_HIERARCHIZE)]:
+        t = torch.zeros(inputs.num_points(levels), dtype=torch.float64, device="cuda")
+        with pytest.raises(gbh.GbhError):
+            gbh.transform(t, levels, op, path=gbh.GBH_PATH_GROUPED)
+
+
 @pytest.mark.parametrize("op", ["h", "d", "a"])
 def test_plain_fixed_point_wide_range(op):
     """Pole groups whose values span many binades, and groups of zeros next to
