@@ -236,7 +236,19 @@ def forms(args, dev, hbm):
             restore=lambda: gbh.transform(t, lv3, gbh.GBH_DEHIERARCHIZE))
     measure("fwd_plain_fp32_6_6_5_5_5", t, lv3, gbh.GBH_HIERARCHIZE, 5, 4, path=gbh.GBH_PATH_PLAIN,
             restore=lambda: gbh.transform(t, lv3, gbh.GBH_DEHIERARCHIZE, path=gbh.GBH_PATH_PLAIN))
-    del t
+    # fp32 error against the fp64 GPU run of the same input, relative to
+    # max|u| (the surpluses of the fp32 and fp64 runs, and the round trip);
+    # the parity tests bound the error against the fp64 oracle
+    t.copy_(torch.from_numpy(u3.astype(np.float32)))
+    ref = t.double()
+    umax = ref.abs().max().item()
+    gbh.transform(ref, lv3, gbh.GBH_HIERARCHIZE)
+    gbh.transform(t, lv3, gbh.GBH_HIERARCHIZE)
+    err_h = (t.double() - ref).abs().max().item() / umax
+    gbh.transform(t, lv3, gbh.GBH_DEHIERARCHIZE)
+    err_rt = (t.double() - torch.from_numpy(u3.astype(np.float32)).to(dev).double()).abs().max().item() / umax
+    out["fwd_fp32_6_6_5_5_5"].update({"rel_err_vs_fp64_gpu": err_h, "round_trip_rel_err": err_rt})
+    del t, ref
     # differentiation batch: adjoint of 16 grids of level (8,8,8)
     lv5, u5 = inputs.cfg5()
     for dt, es, nm in ((torch.float64, 8, "fp64"), (torch.float32, 4, "fp32")):
@@ -315,6 +327,25 @@ def scheme_forms(dev, hbm):
         ms_graph = _ms(lambda: g.replay(), 5, restore=lambda: plan.execute(D))
         out[f"batched_gather_graph_{nm}_d4_n14"] = {"ms": ms_graph, "Gpts_s": P / (ms_graph * 1e-3) / 1e9,
                                                     "status": plan.status()}
+        if dt == torch.float32:
+            # fp32 surpluses and gather against an fp64 run on the same inputs
+            gen = torch.Generator(device=dev).manual_seed(1000)
+            for t in grids:
+                t.uniform_(-1, 1, generator=gen)
+            g64 = [t.double() for t in grids]
+            umax = max(t.abs().max().item() for t in g64)
+            plan64 = gbh.Plan.scheme(4, 14, dtype="torch.float64")
+            plan64.bind(g64)
+            plan64.execute(H)
+            plan.execute(H)
+            err = max((a.double() - b).abs().max().item() for a, b in zip(grids, g64)) / umax
+            sparse64 = torch.empty_like(sparse)
+            plan64.gather(sparse64)
+            plan.gather(sparse)
+            gerr = (sparse - sparse64).abs().max().item() / sparse64.abs().max().item()
+            out[f"batched_{nm}_d4_n14"]["rel_err_vs_fp64_gpu"] = err
+            out[f"gather_{nm}_d4_n14"]["rel_err_vs_fp64_gpu"] = gerr
+            del g64, plan64, sparse64
         del g, grids, sparse, plan
         torch.cuda.empty_cache()
     return out
