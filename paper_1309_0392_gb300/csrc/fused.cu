@@ -93,6 +93,20 @@ struct LaunchParams {
 __host__ __device__ inline unsigned magic_of(int e) { return e == 1 ? 0u : (unsigned)(0xFFFFFFFFu / (unsigned)e) + 1u; }
 __device__ __forceinline__ int udiv(int n, unsigned mag) { return mag ? (int)__umulhi((unsigned)n, mag) : n; }
 
+// plain loads with the L2 fill limited to 64 bytes (isolated elements)
+__device__ __forceinline__ double ld_l2_64(const double *p)
+{
+    double v;
+    asm volatile("ld.global.L2::64B.f64 %0, [%1];\n" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_l2_64(const float *p)
+{
+    float v;
+    asm volatile("ld.global.L2::64B.f32 %0, [%1];\n" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // fixed point <-> fp64
 // ---------------------------------------------------------------------------
@@ -388,7 +402,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_closure(const __grid_constant__
                     const int ee = e + q * T;
                     if (ee < C.V) {
                         const int r = udiv(ee, C.mag[0]);
-                        tmp[q] = u[rowg[r] + (int64_t)(ee - r * e0) * gs0];
+                        const ST *src = u + rowg[r] + (int64_t)(ee - r * e0) * gs0;
+                        tmp[q] = gs0 == 1 ? *src : ld_l2_64(src);
                     }
                 }
 #pragma unroll
@@ -533,6 +548,18 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc)
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+// the same with the L2 fill limited to 64 bytes around the element (isolated
+// elements of a lattice along dimension 0)
+__device__ __forceinline__ void cp_async8_l2_64(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4_l2_64(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -581,8 +608,13 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     for (int e = tid; e < NV; e += T) {
         const int x = e % E0, r = e / E0;
         const ST *src = ub + x * P.gs0 + (r % E1) * P.gs1 + (r / E1) * P.gs2;
-        if constexpr (sizeof(ST) == 8) cp_async8(vals + e, src);
-        else cp_async4(vals + e, src);
+        if constexpr (L0) {
+            if constexpr (sizeof(ST) == 8) cp_async8_l2_64(vals + e, src);
+            else cp_async4_l2_64(vals + e, src);
+        } else {
+            if constexpr (sizeof(ST) == 8) cp_async8(vals + e, src);
+            else cp_async4(vals + e, src);
+        }
     }
     cp_async_commit();
     cp_async_wait_all();

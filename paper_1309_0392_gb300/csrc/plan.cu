@@ -708,14 +708,23 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
     // every load of the tile in flight at once.  Other CTAs wrote this grid's
     // previous phase; the dependency wait (an acquire at gpu scope, then the
     // CTA barrier) orders their released stores before these loads.
+    // runs of pole sets shorter than 64 bytes: L2 fills limited to 64 bytes
+    const bool narrow = Sa > 1 && Gc * (int)sizeof(V) < 64;
     for (int w = tid; w < cnt; w += blockDim.x) {
         int i;
         const unsigned dst = (unsigned)__cvta_generic_to_shared(sv + w);
         const V *src = base + gaddr(w, i);
-        if constexpr (sizeof(V) == 8)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
-        else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+        if (narrow) {
+            if constexpr (sizeof(V) == 8)
+                asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+        } else {
+            if constexpr (sizeof(V) == 8)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -996,6 +1005,20 @@ struct GatherParams {
     int fp64;
 };
 
+// read-only loads of isolated elements, L2 fill limited to 64 bytes
+__device__ __forceinline__ double g_ld64(const double *p)
+{
+    double v;
+    asm("ld.global.nc.L2::64B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float g_ld32(const float *p)
+{
+    float v;
+    asm("ld.global.nc.L2::64B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 constexpr int kGatherPer = 2;                      // points per thread
 constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
 constexpr int kGatherAhead = 4;                    // grids whose loads are in flight together
@@ -1042,8 +1065,8 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
                     f += (rest & ((1ll << sbits[k]) - 1)) * sT[b][k];
                     rest >>= sbits[k];
                 }
-            return P.fp64 ? __ldg(reinterpret_cast<const double *>(sP[b]) + f)
-                          : (double)__ldg(reinterpret_cast<const float *>(sP[b]) + f);
+            return P.fp64 ? g_ld64(reinterpret_cast<const double *>(sP[b]) + f)
+                          : (double)g_ld32(reinterpret_cast<const float *>(sP[b]) + f);
         };
         const int q0 = P.list_off[sb], q1 = P.list_off[sb + 1];
         for (int qb = q0; qb < q1; qb += 256) {
