@@ -708,23 +708,14 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
     // every load of the tile in flight at once.  Other CTAs wrote this grid's
     // previous phase; the dependency wait (an acquire at gpu scope, then the
     // CTA barrier) orders their released stores before these loads.
-    // runs of pole sets shorter than 64 bytes: L2 fills limited to 64 bytes
-    const bool narrow = Sa > 1 && Gc * (int)sizeof(V) < 64;
     for (int w = tid; w < cnt; w += blockDim.x) {
         int i;
         const unsigned dst = (unsigned)__cvta_generic_to_shared(sv + w);
         const V *src = base + gaddr(w, i);
-        if (narrow) {
-            if constexpr (sizeof(V) == 8)
-                asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-        } else {
-            if constexpr (sizeof(V) == 8)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-        }
+        if constexpr (sizeof(V) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
