@@ -775,6 +775,33 @@ struct LatticeParams {
     int64_t N;
 };
 
+template <typename ST, int OP, int LEV>
+__device__ __forceinline__ void lattice_pole(ST *pp, int64_t S)
+{
+    // the pole's 2^LEV + 1 points in registers: every load in flight at once
+    constexpr int n = (1 << LEV) + 1, last = 1 << LEV;
+    ST v[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) v[i] = ld_l2_64(pp + i * S);
+    if constexpr (OP == OP_H) {
+#pragma unroll
+        for (int lev = LEV; lev >= 1; --lev) {
+            const int s = 1 << (LEV - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) v[i] = v[i] - ST(0.5) * (v[i - s] + v[i + s]);
+        }
+    } else {
+#pragma unroll
+        for (int lev = 1; lev <= LEV; ++lev) {
+            const int s = 1 << (LEV - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) v[i] = v[i] + ST(0.5) * (v[i - s] + v[i + s]);
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < last; ++i) pp[i * S] = v[i];
+}
+
 template <typename ST, int OP>
 __global__ void __launch_bounds__(kThreads) k_lattice(const __grid_constant__ LatticeParams L, ST *__restrict__ u)
 {
@@ -799,19 +826,28 @@ __global__ void __launch_bounds__(kThreads) k_lattice(const __grid_constant__ La
             off += coord * L.S[j];
         }
         ST *pp = u + off;
-        const int64_t last = (int64_t)1 << L.lev;
         const int64_t S = L.pstride;
-        if (OP == OP_H) {
-            for (int lev = L.lev; lev >= 1; --lev) {
-                const int64_t s = (int64_t)1 << (L.lev - lev);
-                for (int64_t i = s; i < last; i += 2 * s)
-                    pp[i * S] = pp[i * S] - ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
-            }
-        } else {
-            for (int lev = 1; lev <= L.lev; ++lev) {
-                const int64_t s = (int64_t)1 << (L.lev - lev);
-                for (int64_t i = s; i < last; i += 2 * s)
-                    pp[i * S] = pp[i * S] + ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
+        switch (L.lev) {
+            case 1: lattice_pole<ST, OP, 1>(pp, S); break;
+            case 2: lattice_pole<ST, OP, 2>(pp, S); break;
+            case 3: lattice_pole<ST, OP, 3>(pp, S); break;
+            case 4: lattice_pole<ST, OP, 4>(pp, S); break;
+            case 5: lattice_pole<ST, OP, 5>(pp, S); break;
+            default: {
+                const int64_t last = (int64_t)1 << L.lev;
+                if (OP == OP_H) {
+                    for (int lev = L.lev; lev >= 1; --lev) {
+                        const int64_t s = (int64_t)1 << (L.lev - lev);
+                        for (int64_t i = s; i < last; i += 2 * s)
+                            pp[i * S] = pp[i * S] - ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
+                    }
+                } else {
+                    for (int lev = 1; lev <= L.lev; ++lev) {
+                        const int64_t s = (int64_t)1 << (L.lev - lev);
+                        for (int64_t i = s; i < last; i += 2 * s)
+                            pp[i * S] = pp[i * S] + ST(0.5) * (pp[(i - s) * S] + pp[(i + s) * S]);
+                    }
+                }
             }
         }
     }
