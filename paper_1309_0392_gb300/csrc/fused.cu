@@ -147,14 +147,6 @@ __device__ __forceinline__ long long to_fixed_pc(long long bits, int emaxp)
     return bits < 0 ? -v : v;
 }
 
-// from_fixed with the zero test and the exponent add on the high word.
-__device__ __forceinline__ double from_fixed_hi(long long v, int Xhi32)
-{
-    const double r = __ll2double_rn(v);
-    const int h = __double2hiint(r);
-    return __hiloint2double(h == 0 ? 0 : h + Xhi32, __double2loint(r));
-}
-
 // Out-of-range closures (all values below 2^-960 or near the fp64 maximum):
 // exact but slow conversions.
 __device__ __noinline__ long long to_fixed_slow(long long bits, int emax, int c)
@@ -654,16 +646,25 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
             if constexpr (FIX) w = fast ? to_fixed((long long)w, emax, P_, rbias) : to_fixed_slow((long long)w, emax, cshift);
             v[i] = w;
         }
+        bool changed = OP == OP_H;
         if constexpr (OP == OP_H) {
             pole_regs<V, E0, FIX ? P_H_DBL : P_H_NAT>(v);
         } else if constexpr (L0) {
-            if (inner1(y) && inner2(z)) pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
+            if (inner1(y) && inner2(z)) {
+                pole_regs<V, E0, FIX ? P_D_FIX : P_D_NAT>(v);
+                changed = true;
+            }
         } else if (!(inner1(y) && inner2(z))) {
             pole_regs<V, E0, FIX ? P_H_HALF : P_H_NAT>(v);
+            changed = true;
         }
+        // magnitudes for the renormalisation: rows left as converted stay
+        // below 2^g0, which the OR covers anyway
         if constexpr (OP == OP_D) {
+            if (changed) {
 #pragma unroll
-            for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
+                for (int i = 0; i < E0; ++i) orv |= mag_bits_or(v[i]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
