@@ -632,6 +632,106 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         fast = emax >= 64 && emax <= 1900;
     }
 
+    if constexpr (OP == OP_D && LM == 0 && FIX) {
+        // Interior class, inverse.  The faces of the closure hold nodal
+        // values, its interior surpluses.  Dimension 0 swept over the
+        // interior rows needs the rows' ends (the x faces) hierarchical in
+        // dimensions 1 and 2; dimension 1 over poles with x, z interior needs
+        // their ends (the y faces) hierarchical in dimension 2; dimension 2
+        // needs its ends (the z faces) nodal, as they are.  Stage A brings the
+        // x and y faces there (scale c); stage B converts the interior at the
+        // renormalised scale c - shift as it loads it and sweeps dimensions
+        // 0, 1, 2 over interior poles only.
+        auto cvt = [&](long long bits, int cs, int Pp, int rb) -> long long {
+            return fast ? to_fixed(bits, emax, Pp, rb) : to_fixed_slow(bits, emax, cs);
+        };
+        constexpr int NXF = 2 * E1 * E2, NYF = 2 * (E0 - 2) * E2;
+        for (int w = tid; w < NXF + NYF; w += T) {
+            int e;
+            if (w < NXF) {
+                const int f = w / (E1 * E2), r = w - f * (E1 * E2);
+                e = f * B0 + r * E0;
+            } else {
+                const int w2 = w - NXF, t = w2 / (E0 - 2), x = 1 + w2 - t * (E0 - 2);
+                const int z = t >> 1, f = t & 1;
+                e = x + E0 * (f * B1 + E1 * z);
+            }
+            vals[e] = (V)cvt((long long)vals[e], cshift, P_, rbias);
+        }
+        __syncthreads();
+        unsigned long long ora = (1ull << P.g0) - 1ull;
+        // x faces along y (every z); y faces along z (x interior)
+        for (int p = tid; p < 2 * E2 + 2 * (E0 - 2); p += T) {
+            if (p < 2 * E2) {
+                const int f = p / E2, z = p - f * E2;
+                ora |= pole_smem_or<V, E1, P_H_HALF>(vals + f * B0 + E0 * E1 * z, E0);
+            } else {
+                const int q = p - 2 * E2, f = q & 1, x = 1 + (q >> 1);
+                ora |= pole_smem_or<V, E2, P_H_HALF>(vals + x + E0 * f * B1, E0 * E1);
+            }
+        }
+        __syncthreads();
+        // x faces along z (y interior)
+        for (int p = tid; p < 2 * (E1 - 2); p += T) {
+            const int f = p & 1, y = 1 + (p >> 1);
+            ora |= pole_smem_or<V, E2, P_H_HALF>(vals + f * B0 + E0 * y, E0 * E1);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) ora |= __shfl_xor_sync(0xFFFFFFFFu, ora, o);
+        if ((tid & 31) == 0) atomicOr(&s_or, ora);
+        __syncthreads();
+        int shift = (64 - __clzll((long long)s_or)) + P.growth_bits - 62;
+        shift = shift > 0 ? shift : 0;
+        const int cs2 = cshift - shift, P2s = cs2 > 0 ? cs2 : 0, rb2 = P2s - cs2;
+        X += shift;
+        // stage B, dimension 0: rows with y, z interior
+        for (int r = tid; r < (E1 - 2) * (E2 - 2); r += T) {
+            const int zz = r / (E1 - 2), y = 1 + r - zz * (E1 - 2), z = 1 + zz;
+            V *row = vals + E0 * (y + E1 * z);
+            V v[E0];
+            v[0] = row[0] >> shift;
+            v[B0] = row[B0] >> shift;
+#pragma unroll
+            for (int i = 1; i < B0; ++i) v[i] = (V)cvt((long long)row[i], cs2, P2s, rb2);
+            pole_regs<V, E0, P_D_FIX>(v);
+#pragma unroll
+            for (int i = 1; i < B0; ++i) row[i] = v[i];
+        }
+        __syncthreads();
+        // dimension 1: poles with x, z interior
+        for (int p = tid; p < (E0 - 2) * (E2 - 2); p += T) {
+            const int zz = p / (E0 - 2), x = 1 + p - zz * (E0 - 2), z = 1 + zz;
+            V *sp = vals + x + E0 * E1 * z;
+            V v[E1];
+            v[0] = sp[0] >> shift;
+            v[B1] = sp[B1 * E0] >> shift;
+#pragma unroll
+            for (int i = 1; i < B1; ++i) v[i] = sp[i * E0];
+            pole_regs<V, E1, P_D_FIX>(v);
+#pragma unroll
+            for (int i = 1; i < B1; ++i) sp[i * E0] = v[i];
+        }
+        __syncthreads();
+        // dimension 2: poles with x, y interior; the z faces converted here;
+        // the interior points go to global memory
+        const long long Xhi = (long long)X << 52;
+        for (int p = tid; p < (E0 - 2) * (E1 - 2); p += T) {
+            const int yy = p / (E0 - 2), x = 1 + p - yy * (E0 - 2), y = 1 + yy;
+            V *sp = vals + x + E0 * y;
+            V v[E2];
+            v[0] = (V)cvt((long long)sp[0], cs2, P2s, rb2);
+            v[B2] = (V)cvt((long long)sp[B2 * E0 * E1], cs2, P2s, rb2);
+#pragma unroll
+            for (int i = 1; i < B2; ++i) v[i] = sp[i * E0 * E1];
+            pole_regs<V, E2, P_D_FIX>(v);
+            ST *o = ub + x * P.gs0 + y * P.gs1;
+#pragma unroll
+            for (int i = 1; i < B2; ++i)
+                o[i * P.gs2] = fast ? (ST)from_fixed((long long)v[i], Xhi) : (ST)from_fixed_slow((long long)v[i], X);
+        }
+        return;
+    }
+
     unsigned long long orv = 0ull;
     // stage A of the inverse along one dimension: a lattice dimension
     // dehierarchizes the poles through class points (block coordinates
