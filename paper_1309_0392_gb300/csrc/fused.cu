@@ -770,11 +770,12 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
     }
     __syncthreads();
-    // dimension 1
+    // dimension 1 (hierarchize: the x faces are not needed any more)
     for (int p = tid; p < P1; p += T) {
         const int x = p % E0, z = p / E0;
         V *sp = vals + x + z * E0 * E1;
         if constexpr (OP == OP_H) {
+            if (LM == 0 && !inner0(x)) continue;
             pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
         } else if constexpr (L1) {
             if (inner0(x) && inner2(z)) orv |= pole_smem_or<V, E1, FIX ? P_D_FIX : P_D_NAT>(sp, E0);
@@ -837,6 +838,7 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     const long long Xhi = (long long)X << 52;
     for (int p = tid; p < P2; p += T) {
         const int x = p % E0, y = p / E0;
+        if (!(inner0(x) && inner1(y))) continue;       // nothing of these poles is stored
         V *sp = vals + x + y * E0;
         V v[E2];
 #pragma unroll
