@@ -770,12 +770,13 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
         for (int i = 0; i < E0; ++i) vals[r * E0 + i] = v[i];
     }
     __syncthreads();
-    // dimension 1 (hierarchize: the x faces are not needed any more)
-    for (int p = tid; p < P1; p += T) {
-        const int x = p % E0, z = p / E0;
+    // dimension 1 (hierarchize, interior class: the x faces are not needed
+    // any more, so only poles with x interior, numbered compactly)
+    constexpr int XS = (OP == OP_H && LM == 0) ? 1 : 0, XE = E0 - 2 * XS;
+    for (int p = tid; p < XE * E2; p += T) {
+        const int x = XS + p % XE, z = p / XE;
         V *sp = vals + x + z * E0 * E1;
         if constexpr (OP == OP_H) {
-            if (LM == 0 && !inner0(x)) continue;
             pole_smem<V, E1, FIX ? P_H_DBL : P_H_NAT>(sp, E0);
         } else if constexpr (L1) {
             if (inner0(x) && inner2(z)) orv |= pole_smem_or<V, E1, FIX ? P_D_FIX : P_D_NAT>(sp, E0);
@@ -836,9 +837,10 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     // dimension 2 (hierarchize; block stage of the inverse), then the class
     // points go to global memory
     const long long Xhi = (long long)X << 52;
-    for (int p = tid; p < P2; p += T) {
-        const int x = p % E0, y = p / E0;
-        if (!(inner0(x) && inner1(y))) continue;       // nothing of these poles is stored
+    // only poles whose points are stored, numbered compactly
+    constexpr int X0 = L0 ? 0 : 1, NX = L0 ? E0 : E0 - 2, Y0 = L1 ? 0 : 1, NY = L1 ? E1 : E1 - 2;
+    for (int p = tid; p < NX * NY; p += T) {
+        const int x = X0 + p % NX, y = Y0 + p / NX;
         V *sp = vals + x + y * E0;
         V v[E2];
 #pragma unroll
