@@ -49,10 +49,8 @@ int num_sms();
 
 // Grouped path: one pass per group of consecutive dimensions whose pole sets
 // fit in a shared-memory tile (hierarchize and dehierarchize).  Returns
-// GBH_EUNSUPPORTED for shapes it does not take.  grouped_passes: the number
-// of passes it needs, or -1.
+// GBH_EUNSUPPORTED for shapes it does not take.
 int grouped_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s);
-int grouped_passes(const Geom &g);
 
 // Plain path: one sweep per dimension.  fixed64: fp64 pole groups compute in
 // int64 fixed point (otherwise native arithmetic in the serial operation

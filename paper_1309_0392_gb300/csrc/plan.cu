@@ -1232,19 +1232,6 @@ bool make_grid_info(const Geom &g, GridInfo *gi)
 
 }  // namespace
 
-int grouped_passes(const Geom &g)
-{
-    GridInfo gi;
-    if (!make_grid_info(g, &gi)) return -1;
-    int passes = 0;
-    for (int q = 0; q < gi.ngroups; ++q) {
-        bool any = false;
-        for (int k = gi.grp_lo[q]; k <= gi.grp_hi[q]; ++k) any |= gi.l[k] > 0;
-        passes += any;
-    }
-    return passes;
-}
-
 int grouped_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s)
 {
     if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return GBH_EUNSUPPORTED;
