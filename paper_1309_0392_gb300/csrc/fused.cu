@@ -597,9 +597,12 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     const int64_t by = t % P.nb1, bz = t / P.nb1;
     ST *__restrict__ ub = u + b * P.N + bx * P.step0 + by * P.step1 + bz * P.step2;
     if (tid == 0) { s_emax = 0; s_or = 0ull; }
+    // tile-relative offsets in 32 bits (the host checks that the closure's
+    // span fits)
+    const int g0s = (int)P.gs0, g1s = (int)P.gs1, g2s = (int)P.gs2;
     for (int e = tid; e < NV; e += T) {
         const int x = e % E0, r = e / E0;
-        const ST *src = ub + x * P.gs0 + (r % E1) * P.gs1 + (r / E1) * P.gs2;
+        const ST *src = ub + (x * g0s + (r % E1) * g1s + (r / E1) * g2s);
         if constexpr (L0) {
             if constexpr (sizeof(ST) == 8) cp_async8_l2_64(vals + e, src);
             else cp_async4_l2_64(vals + e, src);
@@ -1348,6 +1351,9 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
         if (c.lev[k] < 1) return 1;
     const int E0 = c.e[0], E1 = c.e[1], E2 = c.e[2], LM = (int)cp.mask;
     if ((size_t)E0 * E1 * E2 * sizeof(ST) > 200 * 1024) return 1;
+    // closure-relative offsets are 32-bit in the kernel
+    if ((double)(E0 - 1) * c.gstride[0] + (double)(E1 - 1) * c.gstride[1] + (double)(E2 - 1) * c.gstride[2] >= 2147483647.0)
+        return 1;
     Tile3Params P{};
     P.S1 = g.S[1];
     P.S2 = g.S[2];
