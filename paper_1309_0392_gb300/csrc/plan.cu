@@ -690,8 +690,11 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
         const int64_t o = fdiv(it.start, gi.divS[lo]);
         base0 = o * Sout + (it.start - o * Sa) + (split ? ((int64_t)it.blk << m) * Sa : 0);
     }
-    // global address of element w of the tile (its shared-memory slot is w)
-    // and its index i within the pole set
+    // offset of element w of the tile from its first point (its shared-memory
+    // slot is w) and its index i within the pole set; 32-bit when the tile's
+    // span allows (every plan grid below 2^31 points)
+    const bool narrow = gi.N < ((int64_t)1 << 31);
+    const int Sout32 = (int)Sout, Sa32 = (int)Sa;
     auto gaddr = [&](int w, int &i) -> int64_t {
         if (contig) {
             i = 0;
@@ -700,10 +703,10 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
         if (Sa == 1) {
             const int g = magM ? (int)__umulhi((unsigned)w, magM) : w;
             i = w - g * M;
-            return base0 + (int64_t)g * Sout + i;
+            return narrow ? base0 + (g * Sout32 + i) : base0 + (int64_t)g * Sout + i;
         }
         i = magG ? (int)__umulhi((unsigned)w, magG) : w;
-        return base0 + (w - i * Gc) + (int64_t)i * Sa;
+        return narrow ? base0 + ((w - i * Gc) + i * Sa32) : base0 + (w - i * Gc) + (int64_t)i * Sa;
     };
     // every load of the tile in flight at once.  Other CTAs wrote this grid's
     // previous phase; the dependency wait (an acquire at gpu scope, then the
