@@ -34,9 +34,10 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_cuda_arm_line():
-    r = run_bench("--steps", "3", "--warmup", "3", "--no-forms", "--no-cpu")
+    # enough steps for the clock sampler (one sample per 200 ms) to see the timed region
+    r = run_bench("--steps", "300", "--warmup", "3", "--no-forms", "--no-cpu")
     assert BASE_KEYS <= set(r)
-    assert r["n_gpus"] == 1 and r["steps"] == 3 and r["warmup"] == 3
+    assert r["n_gpus"] == 1 and r["steps"] == 300 and r["warmup"] == 3
     assert r["higher_is_better"] is True and r["value"] > 0
     assert r["gpu_launches"] > 0
     roof = r["roofline"]
