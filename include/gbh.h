@@ -195,15 +195,21 @@ int gbh_plan_total_points(const gbh_plan *plan, int64_t *out);
 int gbh_plan_bind(gbh_plan *plan, void *const *grid_ptrs, void *stream);
 
 /*
- * Transform every bound grid in place (op = gbh_op) with one persistent
- * kernel launch driven by a device work queue.
+ * Transform every bound grid in place (op = GBH_HIERARCHIZE or
+ * GBH_DEHIERARCHIZE; GBH_EUNSUPPORTED for the transpose) with one persistent
+ * kernel launch driven by a device work queue.  Each grid is transformed group
+ * of dimensions by group of dimensions (consecutive dimensions whose pole sets
+ * fit a shared-memory tile), fp64 in int64 fixed point per tile; results agree
+ * with the single-grid calls within the fp64 / fp32 tolerance.  Stream-ordered;
+ * device-side wait timeouts are reported by gbh_plan_status.
  */
 int gbh_plan_execute(gbh_plan *plan, int op, void *stream);
 
 /*
  * Gather (Sec. 2, "Hierarchization as preprocessing"): sparse[p] = sum over
  * the grids containing p of c_g * alpha_g(p), added in grid enumeration order
- * in fp64, starting from 0.  The grids must hold surpluses (hierarchized).
+ * in fp64, starting from 0, one fused multiply-add per term.  The grids must
+ * hold surpluses (hierarchized).
  * sparse: device array of gbh_plan_sparse_points doubles, subspace-major
  * layout (blocks of hierarchical subspaces j, lexicographic, j_0 most
  * significant; inside a block dimension 0 fastest; level 0 = the two
@@ -215,15 +221,17 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream);
  * Batched transform that allocates nothing, for callers that may not call
  * cudaMalloc (a framework's caching allocator owns the device, a strict memory
  * budget, or a context where allocation is not allowed).  The paper has no
- * counterpart: it is a variant of gbh_plan_execute whose work queue, counters
- * and per-grid tables live in one fixed device array of 4 MiB inside the
- * library (held by every GPU that loads the library until exit) instead of in
- * a plan.
+ * counterpart: a persistent batched kernel like gbh_plan_execute's (one phase
+ * per dimension, int64 fixed point per grid) whose work queue, counters and
+ * per-grid tables live in one fixed device array of 4 MiB inside the library
+ * (held by every GPU that loads the library until exit) instead of in a
+ * plan.
  *   n_grids   : 1..2048 grids; levels: host array [n_grids][d], d in [1, 8]
  *   grid_ptrs : HOST array of n_grids DEVICE pointers (grid g holds
  *               prod_k (2^{l_k}+1) elements of dtype), transformed in place
  *   op        : GBH_HIERARCHIZE or GBH_DEHIERARCHIZE
- * Results are the same as those of a plan for the same grids.  Returns
+ * Results agree with those of a plan for the same grids within the fp64 /
+ * fp32 tolerance.  Returns
  * GBH_ERANGE when the grids need more work items than the array holds
  * (roughly 80,000 items of 65,536 points).  The first call on a device looks
  * up the array's device address; make that call before any stream capture.
