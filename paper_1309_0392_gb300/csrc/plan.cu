@@ -793,7 +793,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
 }
 
 template <typename ST, int OP>
-__global__ void __launch_bounds__(kBThreads, sizeof(ST) == 8 ? kFusedCtas : kFusedCtas + 3) k_fused(const BatchParams P)
+__global__ void __launch_bounds__(kBThreads, sizeof(ST) == 8 ? kFusedCtas + 1 : kFusedCtas + 3) k_fused(const BatchParams P)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_item;
