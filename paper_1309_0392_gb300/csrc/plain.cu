@@ -25,7 +25,7 @@ namespace {
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE, OP_A = GBH_ADJOINT };
 
-constexpr int kRegPoleMaxLevel = 5;      // poles up to 33 points kept in registers
+constexpr int kRegPoleMaxLevel = 5;      // poles up to 33 points kept in registers (65 for fp32)
 constexpr int64_t kMinPolesForThreadPerPole = 152 * 64;
 
 // ---------------------------------------------------------------------------
@@ -446,6 +446,9 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
         return fix ? launch_group<T, OP, sizeof(T) == 8, true>(u, g, 0, st) : launch_group<T, OP, false, true>(u, g, 0, st);
     }
     if (fix && g.n[k] <= kGroupElems) return launch_group<T, OP, sizeof(T) == 8, false>(u, g, k, st);
+    // fp32 poles of 65 points still fit in registers
+    if constexpr (sizeof(T) == 4)
+        if (l == kRegPoleMaxLevel + 1) return launch_pole_regs<T, OP, kRegPoleMaxLevel + 1>(u, g.S[k], poles, st);
     if (l <= kRegPoleMaxLevel) {
         switch (l) {
             case 1: return launch_pole_regs<T, OP, 1>(u, g.S[k], poles, st);
