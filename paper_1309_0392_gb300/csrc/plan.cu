@@ -166,7 +166,9 @@ constexpr int kGroupElems = 8208;               // shared-memory elements per it
 // fused kernel: tile size (elements), CTAs per SM, and the block level of
 // dimensions longer than a tile
 constexpr int kFusedElems = 6144;
-constexpr int kFusedCtas = 3;
+constexpr int kFusedCtas64 = 4;                  // resident CTAs per SM, fp64 / fp32 plans
+constexpr int kFusedCtas32 = 6;
+constexpr int kGroupedCtas = 3;                  // single-grid grouped launches
 constexpr int kSplitLevel = 12;
 
 template <int OP>
@@ -793,7 +795,7 @@ __device__ __forceinline__ void fused_item(const Item &it, const GridInfo &gi, S
 }
 
 template <typename ST, int OP>
-__global__ void __launch_bounds__(kBThreads, sizeof(ST) == 8 ? kFusedCtas + 1 : kFusedCtas + 3) k_fused(const BatchParams P)
+__global__ void __launch_bounds__(kBThreads, sizeof(ST) == 8 ? kFusedCtas64 : kFusedCtas32) k_fused(const BatchParams P)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_item;
@@ -843,7 +845,7 @@ struct GroupLaunch {
 };
 
 template <typename ST, int OP>
-__global__ void __launch_bounds__(kBThreads, kFusedCtas) k_grouped(const __grid_constant__ GroupLaunch L, ST *u)
+__global__ void __launch_bounds__(kBThreads, kGroupedCtas) k_grouped(const __grid_constant__ GroupLaunch L, ST *u)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_em;
