@@ -618,16 +618,12 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     int X = 0, emax = 0, P_ = 0, rbias = 0, cshift = 0;
     bool fast = true;
     if constexpr (FIX) {
-        // largest binary exponent of the closure: the masked high words of two
-        // values per 16-byte load (the exponent field orders like the exponent)
-        const uint4 *q4 = reinterpret_cast<const uint4 *>(vals);
-        unsigned em = 0;
-        for (int e2 = tid; e2 < NV / 2; e2 += T) {
-            const uint4 w = q4[e2];
-            em = max(em, max(w.y & 0x7FF00000u, w.w & 0x7FF00000u));
+        // largest binary exponent of the closure (high words only)
+        const unsigned *hw = reinterpret_cast<const unsigned *>(vals);
+        for (int e = tid; e < NV; e += T) {
+            const int ex = (int)(hw[2 * e + 1] >> 20) & 0x7FF;
+            emax = ex > emax ? ex : emax;
         }
-        if ((NV & 1) && tid == 0) em = max(em, reinterpret_cast<const unsigned *>(vals)[2 * (NV - 1) + 1] & 0x7FF00000u);
-        emax = (int)(em >> 20);
         emax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)emax);
         if ((tid & 31) == 0) atomicMax(&s_emax, emax);
         __syncthreads();
