@@ -67,6 +67,9 @@ def _load():
             lib.orc_gather.restype = None
             lib.orc_gather.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, _DP,
                                        ctypes.POINTER(_DP), _DP]
+            lib.orc_scatter.restype = None
+            lib.orc_scatter.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _IP, _DP, ctypes.c_int,
+                                        _DP, ctypes.POINTER(_DP)]
             lib.orc_level_weights.restype = None
             lib.orc_level_weights.argtypes = [ctypes.c_int, _IP, _DP]
             _lib = lib
@@ -184,6 +187,18 @@ def gather(d: int, n: int, levels, coeffs, grids):
     out = np.zeros(sparse_num_points(d, n), dtype=np.float64)
     _load().orc_gather(d, n, len(gs), lv.ctypes.data_as(_IP), _f64(cf), ptrs, _f64(out))
     return out
+
+
+def scatter(d: int, n: int, levels, coeffs, sparse, scaled: bool = False):
+    """alpha_g = sparse restricted to the points of grid g (times coeffs[g]
+    when scaled: the transpose of gather); one array per grid."""
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32).reshape(-1, d))
+    cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+    sp = np.ascontiguousarray(sparse, dtype=np.float64)
+    outs = [np.zeros(num_points(l), dtype=np.float64) for l in lv]
+    ptrs = (_DP * len(outs))(*[_f64(o) for o in outs])
+    _load().orc_scatter(d, n, len(outs), lv.ctypes.data_as(_IP), _f64(cf), 1 if scaled else 0, _f64(sp), ptrs)
+    return outs
 
 
 def level_weights(levels):

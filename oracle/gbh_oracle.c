@@ -473,6 +473,27 @@ void orc_gather(int d, int n, int ngrids, const int *levels, const double *coeff
     }
 }
 
+/* Scatter, the step back of the iterated combination technique (Sec. 2,
+ * "Hierarchization as preprocessing"): every component grid receives the
+ * combined sparse-grid surpluses of its own points.  Each subspace of grid g
+ * is a subspace of the sparse grid, so point f of grid g takes
+ * sparse[index of f]; dehierarchizing the result gives the combined
+ * sparse-grid function at the points of grid g (hats of finer subspaces vanish
+ * there).  With scaled != 0 the value is multiplied by coeffs[g], one fp64
+ * product, which makes this map the transpose of orc_gather. */
+void orc_scatter(int d, int n, int ngrids, const int *levels, const double *coeffs, int scaled,
+                 const double *sparse, double *const *grids)
+{
+    for (int g = 0; g < ngrids; ++g) {
+        const int *l = levels + (int64_t)g * d;
+        const int64_t N = orc_num_points(d, l);
+        int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * N);
+        orc_sparse_index_of_grid(d, n, l, idx);
+        for (int64_t f = 0; f < N; ++f) grids[g][f] = scaled ? coeffs[g] * sparse[idx[f]] : sparse[idx[f]];
+        free(idx);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Loss weights of the differentiation workload                               */
 /* ------------------------------------------------------------------------ */

@@ -365,6 +365,90 @@ def test_gather_of_one_function_is_its_sparse_surplus(orc, d, n):
         off += size
 
 
+def _sparse_layout(d, n):
+    """Sparse-grid points in subspace-major order, written out from the layout
+    definition: (subspace j, position p, coordinates as Fractions)."""
+    out = []
+    for j in subspaces(d, n):
+        size = int(np.prod([2 if v == 0 else 2 ** (v - 1) for v in j]))
+        for pos in range(size):
+            rem, x, p = pos, [], []
+            for v in j:
+                w = 2 if v == 0 else 2 ** (v - 1)
+                pk = rem % w
+                rem //= w
+                p.append(pk)
+                x.append(Fraction(pk, 1) if v == 0 else Fraction(2 * pk + 1, 2 ** v))
+            out.append((j, tuple(p), tuple(x)))
+    return out
+
+
+@pytest.mark.parametrize("d,n", [(2, 3), (3, 3), (2, 5), (4, 2)])
+@pytest.mark.parametrize("scaled", [False, True])
+def test_scatter_matches_coordinate_dictionary(orc, d, n, scaled):
+    """Every grid point takes the sparse value at its own coordinates."""
+    lv, c = orc.scheme(d, n)
+    layout = _sparse_layout(d, n)
+    where = {x: q for q, (_, _, x) in enumerate(layout)}
+    sparse = np.random.default_rng(11).uniform(-1, 1, len(layout))
+    grids = orc.scatter(d, n, lv, c, sparse, scaled=scaled)
+    for l, cg, g in zip(lv, c, grids):
+        assert g.size == orc.num_points(l)
+        for f in range(g.size):
+            v = sparse[where[_coord_key(l, f)]]
+            assert g[f] == (cg * v if scaled else v)
+
+
+@pytest.mark.parametrize("d,n", [(2, 4), (3, 3), (4, 3)])
+def test_scaled_scatter_is_transpose_of_gather(orc, d, n):
+    """<gather(alpha), s> = sum_g <alpha_g, scatter_scaled(s)_g>, exact on
+    small integers."""
+    lv, c = orc.scheme(d, n)
+    rng = np.random.default_rng(12)
+    alphas = [rng.integers(-8, 9, orc.num_points(l)).astype(np.float64) for l in lv]
+    s = rng.integers(-8, 9, orc.sparse_num_points(d, n)).astype(np.float64)
+    lhs = int(np.dot(orc.gather(d, n, lv, c, alphas).astype(np.int64), s.astype(np.int64)))
+    back = orc.scatter(d, n, lv, c, s, scaled=True)
+    rhs = sum(int(np.dot(a.astype(np.int64), b.astype(np.int64))) for a, b in zip(alphas, back))
+    assert lhs == rhs
+
+
+@pytest.mark.parametrize("d,n", [(2, 4), (3, 4), (4, 3)])
+def test_gather_after_scatter_is_identity(orc, d, n):
+    """Partition of unity: the coefficients of the grids holding a point sum
+    to 1, so gathering the scattered sparse grid returns it (exact on
+    values with few mantissa bits)."""
+    lv, c = orc.scheme(d, n)
+    s = np.random.default_rng(13).integers(-1000, 1001, orc.sparse_num_points(d, n)) / 1024.0
+    assert np.array_equal(orc.gather(d, n, lv, c, orc.scatter(d, n, lv, c, s)), s)
+
+
+@pytest.mark.parametrize("d,n", [(2, 3), (2, 4), (3, 3)])
+def test_iterated_round_gives_sparse_interpolant(orc, d, n):
+    """One round of the iterated combination technique (hierarchize, gather,
+    scatter, dehierarchize) leaves on every grid the combined sparse-grid
+    function at that grid's points, evaluated here as a sum over the sparse
+    hat basis."""
+    fv = lambda *xs: math.prod([np.cos(0.5 + (k + 2) * x) for k, x in enumerate(xs)])
+    lv, c = orc.scheme(d, n)
+    grids = [orc.hierarchize(inputs.sample(l, fv), l) for l in lv]
+    sparse = orc.gather(d, n, lv, c, grids)
+    back = [orc.dehierarchize(g, l) for g, l in zip(orc.scatter(d, n, lv, c, sparse), lv)]
+    layout = _sparse_layout(d, n)
+
+    def hat(j, p, x):
+        if j == 0:
+            return 1.0 - x if p == 0 else x
+        return max(0.0, 1.0 - abs(x - (2 * p + 1) * 2.0 ** -j) * 2.0 ** j)
+
+    for l, g in zip(lv, back):
+        for f in range(g.size):
+            x = [float(v) for v in _coord_key(l, f)]
+            want = sum(sparse[q] * math.prod(hat(j[k], p[k], x[k]) for k in range(d))
+                       for q, (j, p, _) in enumerate(layout))
+            assert g[f] == pytest.approx(want, abs=1e-13)
+
+
 def test_level_weights(orc):
     levels = (2, 1)
     w = orc.level_weights(levels).reshape(3, 5)
