@@ -281,7 +281,9 @@ def _ms(fn, reps, restore=None):
 def scheme_forms(dev, hbm):
     """Batched combination scheme d=4, n=14 (1665 grids, 218.8 M points):
     one persistent launch for all grids, the fp64 gather into the sparse grid
-    (25.4 M points), and both captured in one CUDA graph."""
+    (25.4 M points), the scatter back onto the grids, one iterated round
+    (hierarchize, gather, scatter, dehierarchize), and hierarchize + gather
+    captured in one CUDA graph."""
     import torch
 
     import paper_1309_0392_gb300 as gbh
@@ -311,7 +313,18 @@ def scheme_forms(dev, hbm):
         gb = (es * P + 8 * plan.sparse_points) / (ms_g * 1e-3) / 1e9
         out[f"gather_{nm}_d4_n14"] = {"ms": ms_g, "GB_s": gb, "frac_of_hbm": gb / hbm,
                                       "sparse_points": plan.sparse_points}
-        plan.execute(D)
+        ms_s = _ms(lambda: plan.scatter(sparse), 5)
+        gb = (es * P + 8 * plan.sparse_points) / (ms_s * 1e-3) / 1e9
+        out[f"scatter_{nm}_d4_n14"] = {"ms": ms_s, "GB_s": gb, "frac_of_hbm": gb / hbm}
+
+        def ct_round():
+            # one round of the iterated combination technique
+            plan.execute(H)
+            plan.gather(sparse)
+            plan.scatter(sparse)
+            plan.execute(D)
+        ms_r = _ms(ct_round, 3)
+        out[f"ct_round_{nm}_d4_n14"] = {"ms": ms_r, "Gpts_s": P / (ms_r * 1e-3) / 1e9}
         # one CUDA graph: hierarchize every grid, then gather
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
@@ -532,6 +545,9 @@ def run_case(args):
         if kind == "gather":
             sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
             fn = lambda: plan.gather(sparse)  # noqa: E731
+        if kind == "scatter":
+            sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda").uniform_(-1, 1, generator=gen)
+            fn = lambda: plan.scatter(sparse)  # noqa: E731
     for _ in range(args.warmup):
         fn()
     ms = _ms(fn, max(1, args.steps))

@@ -218,6 +218,35 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream);
 int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream);
 
 /*
+ * Scatter, the step back of the iterated combination technique (Sec. 2,
+ * "Hierarchization as preprocessing"): every bound grid receives the
+ * sparse-grid surpluses of its own points, alpha_g(x) = sparse[p(x)], or
+ * c_g * sparse[p(x)] (one fp64 product) when scaled != 0, which makes the map
+ * the transpose of gbh_plan_gather.  Every subspace of a grid of the scheme is
+ * a subspace of the sparse grid, so every point of every grid is written; a
+ * following gbh_plan_execute(GBH_DEHIERARCHIZE) leaves on each grid the
+ * combined sparse-grid function at that grid's points (hats of finer
+ * subspaces vanish there).
+ *   sparse : device array of gbh_plan_sparse_points doubles in the layout of
+ *            gbh_plan_gather; only read
+ *   scaled : 0 = plain restriction, nonzero = times the grid's coefficient
+ * Scheme plans only (GBH_EUNSUPPORTED otherwise); the grids must be bound
+ * (GBH_EINVAL otherwise).  GBH_F32 grids receive the value rounded to float.
+ * Stream-ordered.
+ */
+int gbh_plan_scatter(gbh_plan *plan, const double *sparse, int scaled, void *stream);
+
+/*
+ * Host only, no GPU: out[f] = position in the sparse grid of the scheme
+ * (d, n) (the layout of gbh_plan_gather) of point f of the grid of level
+ * vector `levels`, for every f < gbh_num_points(d, levels).  The grid must lie
+ * in the sparse grid: 0 <= l_k <= n and sum_k max(l_k, 1) <= n + d - 1
+ * (GBH_ERANGE otherwise).  d in [1, 8], n in [1, 30] (GBH_EINVAL otherwise).
+ * out: host array owned by the caller.
+ */
+int gbh_sparse_index_of_grid(int d, int n, const int32_t *levels, int64_t *out);
+
+/*
  * Batched transform that allocates nothing, for callers that may not call
  * cudaMalloc (a framework's caching allocator owns the device, a strict memory
  * budget, or a context where allocation is not allowed).  The paper has no

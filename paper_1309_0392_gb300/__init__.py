@@ -13,10 +13,10 @@ import ctypes
 from . import _lib
 from ._lib import (GBH_ADJOINT, GBH_DEHIERARCHIZE, GBH_HIERARCHIZE, GBH_PATH_AUTO,  # noqa: F401
                    GBH_PATH_FUSED, GBH_PATH_GROUPED, GBH_PATH_PLAIN, GBH_ARITH_AUTO, GBH_ARITH_NATIVE,
-                   GBH_ARITH_FIXED, GbhError)
+                   GBH_ARITH_FIXED, GbhError, sparse_index_of_grid)
 
 __all__ = ["hierarchize", "dehierarchize", "hierarchize_adjoint", "transform", "num_points",
-           "Plan", "HierarchizeFn", "GbhError"]
+           "Plan", "HierarchizeFn", "GbhError", "sparse_index_of_grid"]
 
 
 def num_points(levels) -> int:

@@ -62,6 +62,9 @@ _SIGS = {
     "gbh_plan_bind": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), _VP]),
     "gbh_plan_execute": (ctypes.c_int, [_VP, ctypes.c_int, _VP]),
     "gbh_plan_gather": (ctypes.c_int, [_VP, _VP, _VP]),
+    "gbh_plan_scatter": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    "gbh_sparse_index_of_grid": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P,
+                                                ctypes.POINTER(ctypes.c_int64)]),
     "gbh_plan_status": (ctypes.c_int, [_VP, _VP]),
     "gbh_plan_test_stall": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
     "gbh_batched_transform_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P, ctypes.POINTER(_VP),
@@ -141,6 +144,23 @@ def profile_read():
             break
         out[buf.value.decode()] = (int(n.value), float(ms.value), float(by.value))
         i += 1
+    return out
+
+
+def sparse_index_of_grid(d: int, n: int, levels):
+    """Sparse-grid position of every point of grid `levels` in the scheme
+    (d, n) (int64 numpy array, flat grid order).  Host only."""
+    import numpy as np
+    lv = [int(v) for v in levels]
+    if len(lv) != d:
+        raise ValueError("one level per dimension")
+    N = 1
+    for v in lv:
+        N *= (1 << v) + 1
+    out = np.empty(N, dtype=np.int64)
+    check(lib().gbh_sparse_index_of_grid(d, n, levels_arg(lv),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+          "gbh_sparse_index_of_grid")
     return out
 
 

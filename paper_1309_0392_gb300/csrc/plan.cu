@@ -1123,6 +1123,182 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
     }
 }
 
+// ---------------------------------------------------------------------------
+// scatter from the sparse grid back onto the grids
+// ---------------------------------------------------------------------------
+
+// Position of a subspace block in the sparse grid without a table over all
+// subspaces.  With T = n + d - 1 and omega(0) = 2, omega(j) = 2^{j-1} points
+// per dimension, let C_k(b) be the number of points of all suffixes
+// (j_k, ..., j_{d-1}) with sum_{m>=k} max(j_m, 1) <= b.  Blocks before j in
+// lexicographic order (j_0 most significant) agree with j on j_0..j_{k-1} and
+// have a smaller j_k for exactly one k, so
+//   offset(j) = sum_k W_k R_k(j_k, b_k),  W_k = prod_{m<k} omega(j_m),
+//   R_k(jj, b) = sum_{j' < jj} omega(j') C_{k+1}(b - max(j', 1)),
+// with b_0 = T and b_{k+1} = b_k - max(j_k, 1).  rank[(k (n+1) + jj) (T+1) + b]
+// holds R_k(jj, b).
+std::vector<int64_t> build_rank(int d, int n)
+{
+    const int T = n + d - 1, nj = n + 1, nb = T + 1;
+    auto omega = [](int j) -> int64_t { return j == 0 ? 2 : (int64_t)1 << (j - 1); };
+    std::vector<int64_t> C((size_t)(d + 1) * nb, 0), R((size_t)d * nj * nb, 0);
+    for (int b = 0; b < nb; ++b) C[(size_t)d * nb + b] = 1;
+    for (int k = d - 1; k >= 0; --k)
+        for (int b = 0; b < nb; ++b) {
+            int64_t acc = 0;
+            for (int jj = 0; jj < nj; ++jj) {
+                R[((size_t)k * nj + jj) * nb + b] = acc;
+                const int r = b - std::max(jj, 1);
+                if (r >= 0) acc += omega(jj) * C[(size_t)(k + 1) * nb + r];
+            }
+            C[(size_t)k * nb + b] = acc;
+        }
+    return R;
+}
+
+// Sparse-grid position contributed by dimension k of a point with index i on
+// level l: subspace j_k = l - ctz(i) (0 at the two boundary points) and
+// position p_k with i = (2 p_k + 1) 2^{l - j_k} (p_k = 0, 1 at the boundary),
+// dimension 0 fastest inside a block.  Updates the budget b and the block
+// weight W for the next dimension.
+__host__ __device__ __forceinline__ void level_pos(int l, int i, int &j, int &p)
+{
+    if (i == 0 || i == (1 << l)) {
+        j = 0;
+        p = i != 0;
+    } else {
+#ifdef __CUDA_ARCH__
+        const int tz = __ffs(i) - 1;
+#else
+        const int tz = __builtin_ctz((unsigned)i);
+#endif
+        j = l - tz;
+        p = i >> (tz + 1);
+    }
+}
+
+__host__ __device__ __forceinline__ int64_t sparse_pos(int k, int l, int i, int nj, int nb, const int64_t *rank,
+                                                       int &b, int64_t &W)
+{
+    int j, p;
+    level_pos(l, i, j, p);
+    const int64_t add = W * (rank[(k * nj + j) * nb + b] + p);
+    W *= j == 0 ? 2 : (int64_t)1 << (j - 1);
+    b -= j > 1 ? j : 1;
+    return add;
+}
+
+// Position of a point from its dimension-0 part and the part of the other
+// dimensions: with m = max(j_0, 1), out_m = sum_{k>=1} W'_k (R_k(j_k, b_k) + p_k)
+// taken with b_1 = T - m and W'_1 = 1, the position is
+// R_0(j_0, T) + p_0 + omega(j_0) out_m.
+__host__ __device__ __forceinline__ int64_t point_pos(const int64_t *rank, int nb, int T, int j0, int p0,
+                                                      int64_t out_m)
+{
+    return rank[j0 * nb + T] + p0 + (out_m << (j0 == 0 ? 1 : j0 - 1));
+}
+
+struct ScatterParams {
+    int d, nj, nb, T;
+    const int64_t *rank;          // [d][n+1][T+1]
+    int rank_len, max_entries;    // shared-memory layout
+    const int64_t *chunk_first;   // [G+1] first chunk of every grid
+    int ngrids;
+    int64_t nchunks;
+    const GridInfo *grids;
+    void *const *ptrs;
+    const double *coeffs;
+    const double *sparse;
+    int scaled, fp64;
+};
+
+constexpr int kScatterPer = 8;                       // points per thread
+constexpr int kScatterChunk = kScatterPer * 256;     // points per CTA chunk
+
+// Outer parts a chunk needs: the rows it touches times the values of
+// max(j_0, 1) on level l0.
+inline int scatter_entries(int l0)
+{
+    const int n0 = (1 << l0) + 1;
+    return ((kScatterChunk - 1) / n0 + 2) * (l0 > 0 ? l0 : 1);
+}
+
+// A CTA takes a chunk of consecutive points of one grid.  First its threads
+// compute, for every row (dimension-0 pole) the chunk touches and every
+// value of max(j_0, 1), the part of the position due to dimensions >= 1; then
+// thread t writes points t, t + 256, ... (coalesced), each resolving only its
+// dimension-0 level, with all eight loads issued before the stores.
+// Consecutive points of one level along dimension 0 read consecutive
+// positions.
+__global__ void __launch_bounds__(256) k_scatter(const ScatterParams P)
+{
+    extern __shared__ int64_t s_rank[];
+    int64_t *s_out = s_rank + P.rank_len;
+    for (int e = threadIdx.x; e < P.rank_len; e += blockDim.x) s_rank[e] = P.rank[e];
+    __syncthreads();
+    const int d = P.d;
+    for (int64_t c = blockIdx.x; c < P.nchunks; c += gridDim.x) {
+        int lo = 0, hi = P.ngrids;                 // chunk_first[lo] <= c < chunk_first[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (P.chunk_first[mid] <= c) lo = mid; else hi = mid;
+        }
+        const GridInfo &gi = P.grids[lo];
+        const int l0 = gi.l[0], n0 = (1 << l0) + 1, nbud = l0 > 0 ? l0 : 1;
+        const int64_t N = gi.N;
+        const int64_t f0 = (c - P.chunk_first[lo]) * kScatterChunk;
+        const int64_t f1 = f0 + kScatterChunk < N ? f0 + kScatterChunk : N;
+        const int64_t ra = f0 / n0;
+        const int nent = (int)((f1 - 1) / n0 - ra + 1) * nbud;
+        for (int e = threadIdx.x; e < nent; e += blockDim.x) {
+            const int rr = e / nbud, m = e - rr * nbud + 1;
+            const int64_t fr = (ra + rr) * n0;     // first point of the row
+            int64_t out = 0, W = 1;
+            int b = P.T - m;
+            for (int k = 1; k < d; ++k) {
+                const int64_t q = fdiv(fr, gi.divS[k]);
+                const int64_t q1 = k + 1 < d ? fdiv(fr, gi.divS[k + 1]) : 0;
+                out += sparse_pos(k, gi.l[k], (int)(q - q1 * (((int64_t)1 << gi.l[k]) + 1)), P.nj, P.nb, s_rank,
+                                  b, W);
+            }
+            s_out[e] = out;
+        }
+        __syncthreads();
+        const double cg = P.scaled ? P.coeffs[lo] : 1.0;
+        const unsigned mag = magic_u32(n0);
+        int64_t idx[kScatterPer];
+#pragma unroll
+        for (int r = 0; r < kScatterPer; ++r) {
+            const int64_t f = f0 + r * 256 + threadIdx.x;
+            idx[r] = -1;
+            if (f < f1) {
+                // t < kScatterChunk + n0; t n0 < 2^32 whenever n0 <= kScatterChunk,
+                // and a longer row leaves t / n0 in {0, 1}
+                const int t = (int)(f - ra * n0);
+                const int rr = n0 > kScatterChunk ? (t >= n0) : (int)__umulhi((unsigned)t, mag);
+                int j0, p0;
+                level_pos(l0, t - rr * n0, j0, p0);
+                const int m = j0 > 1 ? j0 : 1;
+                idx[r] = point_pos(s_rank, P.nb, P.T, j0, p0, s_out[rr * nbud + m - 1]);
+            }
+        }
+        double v[kScatterPer];
+#pragma unroll
+        for (int r = 0; r < kScatterPer; ++r) v[r] = idx[r] >= 0 ? __ldg(P.sparse + idx[r]) : 0.0;
+        void *dst = P.ptrs[lo];
+#pragma unroll
+        for (int r = 0; r < kScatterPer; ++r) {
+            const int64_t f = f0 + r * 256 + threadIdx.x;
+            if (idx[r] >= 0) {
+                const double w = P.scaled ? cg * v[r] : v[r];
+                if (P.fp64) reinterpret_cast<double *>(dst)[f] = w;
+                else reinterpret_cast<float *>(dst)[f] = (float)w;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 double dgrowth(int lev)
 {
     const int n = (1 << lev) + 1;
@@ -1274,6 +1450,11 @@ struct gbh_plan {
     int *d_sub_j = nullptr, *d_list_off = nullptr, *d_list = nullptr;
     int2 *d_chunks = nullptr;
     int nsub = 0, nchunks = 0;
+    int64_t *d_rank = nullptr;        // scatter: subspace ranking table [d][n+1][n+d]
+    int64_t *d_scat_first = nullptr;  // scatter: first chunk of every grid [G+1]
+    int64_t nscat = 0;
+    int rank_len = 0;
+    int scat_entries = 0;             // scatter: largest outer-part table of a chunk
     void **h_ptrs = nullptr;          // pinned staging for bind
     bool bound = false;
     int dev = 0;
@@ -1299,6 +1480,8 @@ void free_plan(gbh_plan *p)
     cudaFree(p->d_list_off);
     cudaFree(p->d_list);
     cudaFree(p->d_chunks);
+    cudaFree(p->d_rank);
+    cudaFree(p->d_scat_first);
     if (p->h_ptrs) cudaFreeHost(p->h_ptrs);
     delete p;
 }
@@ -1477,6 +1660,16 @@ int build_sparse(gbh_plan *p)
     if (int e = upload(&p->d_sub_j, js)) return e;
     if (int e = upload(&p->d_list_off, loff)) return e;
     if (int e = upload(&p->d_list, list)) return e;
+    const std::vector<int64_t> rank = build_rank(d, n);
+    p->rank_len = (int)rank.size();
+    std::vector<int64_t> first(p->ngrids + 1, 0);
+    for (int g = 0; g < p->ngrids; ++g) {
+        first[g + 1] = first[g] + (p->info[g].N + kScatterChunk - 1) / kScatterChunk;
+        p->scat_entries = std::max(p->scat_entries, scatter_entries(p->info[g].l[0]));
+    }
+    p->nscat = first[p->ngrids];
+    if (int e = upload(&p->d_rank, rank)) return e;
+    if (int e = upload(&p->d_scat_first, first)) return e;
     return GBH_OK;
 }
 
@@ -1703,6 +1896,74 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
     ps.done();
     count_launches(1);
     return check_launch();
+}
+
+int gbh_plan_scatter(gbh_plan *plan, const double *sparse, int scaled, void *stream)
+{
+    if (!plan || !sparse) return GBH_EINVAL;
+    if (plan->n < 0) return GBH_EUNSUPPORTED;
+    if (!plan->bound) return GBH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(sparse) % 8) return GBH_EALIGN;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ScatterParams P{};
+    P.d = plan->d;
+    P.T = plan->n + plan->d - 1;
+    P.nj = plan->n + 1;
+    P.nb = P.T + 1;
+    P.rank = plan->d_rank;
+    P.rank_len = plan->rank_len;
+    P.max_entries = plan->scat_entries;
+    P.chunk_first = plan->d_scat_first;
+    P.ngrids = plan->ngrids;
+    P.nchunks = plan->nscat;
+    P.grids = plan->d_info;
+    P.ptrs = plan->d_ptrs;
+    P.coeffs = plan->d_coeffs;
+    P.sparse = sparse;
+    P.scaled = scaled != 0;
+    P.fp64 = plan->dtype == GBH_F64;
+    const size_t smem = sizeof(int64_t) * ((size_t)plan->rank_len + plan->scat_entries);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GBH_ECUDA;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(P.nchunks, (int64_t)num_sms() * 8));
+    ProfScope ps("scatter", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * plan->sparse_points);
+    k_scatter<<<(int)grid, 256, smem, s>>>(P);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+int gbh_sparse_index_of_grid(int d, int n, const int32_t *levels, int64_t *out)
+{
+    if (!levels || !out) return GBH_EINVAL;
+    if (d < 1 || d > kPlanMaxD || n < 1 || n > 30) return GBH_EINVAL;
+    int t = 0;
+    int64_t N = 1, S[kPlanMaxD];
+    for (int k = 0; k < d; ++k) {
+        if (levels[k] < 0 || levels[k] > n) return GBH_ERANGE;
+        t += std::max(levels[k], 1);
+        S[k] = N;
+        const int64_t nk = ((int64_t)1 << levels[k]) + 1;
+        if (N > INT64_MAX / 8 / nk) return GBH_ERANGE;
+        N *= nk;
+    }
+    if (t > n + d - 1) return GBH_ERANGE;
+    const std::vector<int64_t> rank = build_rank(d, n);
+    const int nj = n + 1, nb = n + d, T = n + d - 1;
+    const int64_t n0 = ((int64_t)1 << levels[0]) + 1;
+    for (int64_t f = 0; f < N; ++f) {
+        int j0, p0;
+        level_pos(levels[0], (int)(f % n0), j0, p0);
+        int64_t out_m = 0, W = 1;
+        int b = T - std::max(j0, 1);
+        for (int k = 1; k < d; ++k) {
+            const int i = (int)((f / S[k]) % (((int64_t)1 << levels[k]) + 1));
+            out_m += sparse_pos(k, levels[k], i, nj, nb, rank.data(), b, W);
+        }
+        out[f] = point_pos(rank.data(), nb, T, j0, p0, out_m);
+    }
+    return GBH_OK;
 }
 
 int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit)

@@ -1,5 +1,6 @@
 """Combination-scheme plans: batched transform of many grids in one persistent
-launch, and the fp64 gather into the sparse grid (Sec. 2)."""
+launch, the fp64 gather into the sparse grid and the scatter back onto the
+grids (Sec. 2)."""
 from __future__ import annotations
 
 import ctypes
@@ -98,12 +99,28 @@ class Plan:
         _lib.check(_lib.lib().gbh_plan_execute(self._h, int(op), ctypes.c_void_p(s.cuda_stream)),
                    "gbh_plan_execute")
 
+    def _check_sparse(self, sparse):
+        import torch
+        if not (isinstance(sparse, torch.Tensor) and sparse.is_cuda and sparse.dtype == torch.float64
+                and sparse.is_contiguous() and sparse.numel() == self.sparse_points):
+            raise ValueError(f"sparse must be a contiguous float64 CUDA tensor of {self.sparse_points} points")
+
     def gather(self, sparse, stream=None):
         import torch
+        self._check_sparse(sparse)
         s = stream if stream is not None else torch.cuda.current_stream()
         _lib.check(_lib.lib().gbh_plan_gather(self._h, ctypes.c_void_p(sparse.data_ptr()),
                                               ctypes.c_void_p(s.cuda_stream)), "gbh_plan_gather")
         return sparse
+
+    def scatter(self, sparse, scaled: bool = False, stream=None):
+        """Every bound grid receives the sparse-grid surpluses of its points
+        (times its coefficient when scaled: the transpose of gather)."""
+        import torch
+        self._check_sparse(sparse)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _lib.check(_lib.lib().gbh_plan_scatter(self._h, ctypes.c_void_p(sparse.data_ptr()), 1 if scaled else 0,
+                                               ctypes.c_void_p(s.cuda_stream)), "gbh_plan_scatter")
 
     def test_stall(self, grid: int, spin_limit: int = 1 << 14):
         """Failure injection: the grid's work items wait on a dependency that

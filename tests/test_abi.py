@@ -66,3 +66,40 @@ def test_python_layer_rejects_host_tensors():
     t = torch.zeros(25, dtype=torch.float64)
     with pytest.raises(ValueError):
         gbh.hierarchize(t, (2, 2))
+
+
+@pytest.mark.parametrize("d,n", [(1, 6), (2, 5), (3, 4), (4, 4), (5, 3), (8, 2)])
+def test_sparse_index_of_grid_matches_oracle(L, d, n):
+    """The library's subspace ranking (the index the scatter kernel uses) gives
+    the oracle's sparse-grid position for every point of every grid."""
+    import numpy as np
+    import oracle
+    lv, _ = oracle.scheme(d, n)
+    seen = np.zeros(oracle.sparse_num_points(d, n), dtype=bool)
+    for l in lv:
+        got = gbh.sparse_index_of_grid(d, n, l)
+        assert np.array_equal(got, oracle.sparse_index_of_grid(d, n, l))
+        seen[got] = True
+    assert seen.all()          # the scheme covers the sparse grid
+    # a grid inside the sparse grid that is not in the scheme
+    small = [1] * d
+    assert np.array_equal(gbh.sparse_index_of_grid(d, n, small), oracle.sparse_index_of_grid(d, n, small))
+
+
+def test_sparse_index_of_grid_full_scheme_sampled(L):
+    """The 4-d level-14 scheme (1665 grids): sampled grids, bit-exact."""
+    import numpy as np
+    import oracle
+    lv, _ = oracle.scheme(4, 14)
+    rng = np.random.default_rng(3)
+    for g in sorted(set(int(v) for v in rng.choice(len(lv), 6, replace=False)) | {0, len(lv) - 1}):
+        assert np.array_equal(gbh.sparse_index_of_grid(4, 14, lv[g]), oracle.sparse_index_of_grid(4, 14, lv[g]))
+
+
+def test_sparse_index_of_grid_rejects_grids_outside(L):
+    out = (ctypes.c_int64 * 64)()
+    assert L.gbh_sparse_index_of_grid(2, 3, _lib.levels_arg([4, 1]), out) == -4   # level above n
+    assert L.gbh_sparse_index_of_grid(2, 3, _lib.levels_arg([3, 2]), out) == -4   # |l| too large
+    assert L.gbh_sparse_index_of_grid(0, 3, _lib.levels_arg([1]), out) == -1
+    assert L.gbh_sparse_index_of_grid(9, 3, _lib.levels_arg([1] * 9), out) == -1
+    assert L.gbh_sparse_index_of_grid(2, 0, _lib.levels_arg([0, 0]), out) == -1
