@@ -1177,13 +1177,14 @@ __host__ __device__ __forceinline__ void level_pos(int l, int i, int &j, int &p)
     }
 }
 
-__host__ __device__ __forceinline__ int64_t sparse_pos(int k, int l, int i, int nj, int nb, const int64_t *rank,
-                                                       int &b, int64_t &W)
+template <typename IDX>
+__host__ __device__ __forceinline__ IDX sparse_pos(int k, int l, int i, int nj, int nb, const IDX *rank, int &b,
+                                                   IDX &W)
 {
     int j, p;
     level_pos(l, i, j, p);
-    const int64_t add = W * (rank[(k * nj + j) * nb + b] + p);
-    W *= j == 0 ? 2 : (int64_t)1 << (j - 1);
+    const IDX add = W * (rank[(k * nj + j) * nb + b] + p);
+    W <<= j == 0 ? 1 : j - 1;
     b -= j > 1 ? j : 1;
     return add;
 }
@@ -1192,18 +1193,32 @@ __host__ __device__ __forceinline__ int64_t sparse_pos(int k, int l, int i, int 
 // dimensions: with m = max(j_0, 1), out_m = sum_{k>=1} W'_k (R_k(j_k, b_k) + p_k)
 // taken with b_1 = T - m and W'_1 = 1, the position is
 // R_0(j_0, T) + p_0 + omega(j_0) out_m.
-__host__ __device__ __forceinline__ int64_t point_pos(const int64_t *rank, int nb, int T, int j0, int p0,
-                                                      int64_t out_m)
+template <typename IDX>
+__host__ __device__ __forceinline__ IDX point_pos(const IDX *rank, int nb, int T, int j0, int p0, IDX out_m)
 {
     return rank[j0 * nb + T] + p0 + (out_m << (j0 == 0 ? 1 : j0 - 1));
 }
 
+// A chunk of consecutive points of one grid, with the sizes of its tables
+// and the 32-bit reciprocals its threads divide by (computed on the host).
+struct ScatterChunk {
+    int grid;
+    int t0;          // first point's index along dimension 0
+    int npts;        // points (<= kScatterChunk)
+    int nent;        // parts of dimensions >= 1: rows x values of max(j_0, 1)
+    int nent2;       // parts of dimensions >= 2: planes x values of max(j_0, 1) + max(j_1, 1)
+    int nbud, nb2;   // values of max(j_0, 1); of max(j_0, 1) + max(j_1, 1)
+    int n0;
+    unsigned mag0, magb, magb2, pad;
+    int64_t row;     // first point's row (pole along dimension 0)
+    int64_t plane;   // first row's plane (dimensions 0 and 1)
+};
+
 struct ScatterParams {
     int d, nj, nb, T;
     const int64_t *rank;          // [d][n+1][T+1]
-    int rank_len, max_entries;    // shared-memory layout
-    const int64_t *chunk_first;   // [G+1] first chunk of every grid
-    int ngrids;
+    int rank_len, max_ent;        // shared-memory layout: rank, parts >= 1, parts >= 2
+    const ScatterChunk *chunks;
     int64_t nchunks;
     const GridInfo *grids;
     void *const *ptrs;
@@ -1215,85 +1230,128 @@ struct ScatterParams {
 constexpr int kScatterPer = 8;                       // points per thread
 constexpr int kScatterChunk = kScatterPer * 256;     // points per CTA chunk
 
-// Outer parts a chunk needs: the rows it touches times the values of
-// max(j_0, 1) on level l0.
-inline int scatter_entries(int l0)
+// t / n0 for t < n0 + kScatterChunk: exact by the 32-bit reciprocal when
+// n0 <= kScatterChunk (t n0 < 2^32), and in {0, 1} for longer rows.
+__host__ __device__ __forceinline__ int div_row(int t, int n0, unsigned mag)
 {
-    const int n0 = (1 << l0) + 1;
-    return ((kScatterChunk - 1) / n0 + 2) * (l0 > 0 ? l0 : 1);
+#ifdef __CUDA_ARCH__
+    return n0 > kScatterChunk ? (t >= n0) : (int)__umulhi((unsigned)t, mag);
+#else
+    return n0 > kScatterChunk ? (t >= n0) : (int)(((uint64_t)(unsigned)t * mag) >> 32);
+#endif
 }
 
-// A CTA takes a chunk of consecutive points of one grid.  First its threads
-// compute, for every row (dimension-0 pole) the chunk touches and every
-// value of max(j_0, 1), the part of the position due to dimensions >= 1; then
-// thread t writes points t, t + 256, ... (coalesced), each resolving only its
-// dimension-0 level, with all eight loads issued before the stores.
+// Tables of one chunk.  With l0' = max(l_0, 1) and l1' = max(l_1, 1): the
+// rows it touches times l0' values of max(j_0, 1), and the planes those rows
+// touch times l0' + l1' - 1 values of max(j_0, 1) + max(j_1, 1).
+ScatterChunk make_chunk(int g, const int *l, int d, int64_t N, int64_t f0)
+{
+    ScatterChunk c{};
+    const int64_t n0 = ((int64_t)1 << l[0]) + 1;
+    const int64_t n1 = d > 1 ? ((int64_t)1 << l[1]) + 1 : 1;
+    c.grid = g;
+    c.n0 = (int)n0;
+    c.t0 = (int)(f0 % n0);
+    c.row = f0 / n0;
+    c.npts = (int)std::min<int64_t>(kScatterChunk, N - f0);
+    const int64_t rows = (f0 + c.npts - 1) / n0 - c.row + 1;
+    c.plane = c.row / n1;
+    const int64_t planes = (c.row + rows - 1) / n1 - c.plane + 1;
+    c.nbud = std::max(l[0], 1);
+    c.nb2 = d > 2 ? c.nbud + std::max(l[1], 1) - 1 : 0;
+    c.nent = (int)rows * c.nbud;
+    c.nent2 = d > 2 ? (int)planes * c.nb2 : 0;
+    c.mag0 = magic_u32((int)std::min<int64_t>(n0, 1 << 30));
+    c.magb = magic_u32(c.nbud);
+    c.magb2 = c.nb2 > 0 ? magic_u32(c.nb2) : 0;
+    return c;
+}
+
+// A CTA takes a chunk of consecutive points of one grid.  Its threads first
+// compute the part of the position due to dimensions >= 2 for every plane
+// the chunk touches and every budget those dimensions can have, then from it
+// the part due to dimensions >= 1 for every row and value of max(j_0, 1);
+// then thread t writes points t, t + 256, ... (coalesced), each resolving
+// only its dimension-0 level, with all eight loads issued before the stores.
 // Consecutive points of one level along dimension 0 read consecutive
-// positions.
+// positions.  IDX = int when every position fits in 31 bits.
+template <typename IDX>
 __global__ void __launch_bounds__(256) k_scatter(const ScatterParams P)
 {
-    extern __shared__ int64_t s_rank[];
-    int64_t *s_out = s_rank + P.rank_len;
-    for (int e = threadIdx.x; e < P.rank_len; e += blockDim.x) s_rank[e] = P.rank[e];
+    extern __shared__ int64_t s_mem[];
+    IDX *s_rank = reinterpret_cast<IDX *>(s_mem);
+    IDX *s_out = s_rank + P.rank_len;
+    IDX *s_out2 = s_out + P.max_ent;
+    for (int e = threadIdx.x; e < P.rank_len; e += blockDim.x) s_rank[e] = (IDX)P.rank[e];
     __syncthreads();
     const int d = P.d;
     for (int64_t c = blockIdx.x; c < P.nchunks; c += gridDim.x) {
-        int lo = 0, hi = P.ngrids;                 // chunk_first[lo] <= c < chunk_first[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (P.chunk_first[mid] <= c) lo = mid; else hi = mid;
+        const ScatterChunk ch = P.chunks[c];
+        const GridInfo &gi = P.grids[ch.grid];
+        const int l0 = gi.l[0], n0 = ch.n0, nbud = ch.nbud;
+        // parts of dimensions >= 2, per plane and value s = max(j_0,1) + max(j_1,1)
+        for (int e = threadIdx.x; e < ch.nent2; e += blockDim.x) {
+            const int pp = ch.magb2 ? (int)__umulhi((unsigned)e, ch.magb2) : e, s = e - pp * ch.nb2 + 2;
+            const int64_t plane = ch.plane + pp, fp = plane * gi.S[2];   // first point of the plane
+            IDX out = 0, W = 1;
+            int b = P.T - s;
+            int64_t q = plane;                     // fp / S_2
+            for (int k = 2; k < d; ++k) {
+                const int64_t q1 = k + 1 < d ? fdiv(fp, gi.divS[k + 1]) : 0;
+                out += sparse_pos<IDX>(k, gi.l[k], (int)(q - q1 * (((int64_t)1 << gi.l[k]) + 1)), P.nj, P.nb,
+                                       s_rank, b, W);
+                q = q1;
+            }
+            s_out2[e] = out;
         }
-        const GridInfo &gi = P.grids[lo];
-        const int l0 = gi.l[0], n0 = (1 << l0) + 1, nbud = l0 > 0 ? l0 : 1;
-        const int64_t N = gi.N;
-        const int64_t f0 = (c - P.chunk_first[lo]) * kScatterChunk;
-        const int64_t f1 = f0 + kScatterChunk < N ? f0 + kScatterChunk : N;
-        const int64_t ra = f0 / n0;
-        const int nent = (int)((f1 - 1) / n0 - ra + 1) * nbud;
-        for (int e = threadIdx.x; e < nent; e += blockDim.x) {
-            const int rr = e / nbud, m = e - rr * nbud + 1;
-            const int64_t fr = (ra + rr) * n0;     // first point of the row
-            int64_t out = 0, W = 1;
-            int b = P.T - m;
-            for (int k = 1; k < d; ++k) {
-                const int64_t q = fdiv(fr, gi.divS[k]);
-                const int64_t q1 = k + 1 < d ? fdiv(fr, gi.divS[k + 1]) : 0;
-                out += sparse_pos(k, gi.l[k], (int)(q - q1 * (((int64_t)1 << gi.l[k]) + 1)), P.nj, P.nb, s_rank,
-                                  b, W);
+        if (d > 2) __syncthreads();
+        // parts of dimensions >= 1, per row and value m = max(j_0, 1)
+        for (int e = threadIdx.x; e < ch.nent; e += blockDim.x) {
+            const int rr = ch.magb ? (int)__umulhi((unsigned)e, ch.magb) : e, m = e - rr * nbud + 1;
+            IDX out = 0;
+            if (d > 1) {
+                const int64_t row = ch.row + rr;
+                const int64_t plane = d > 2 ? fdiv(row * n0, gi.divS[2]) : 0;
+                const int l1 = gi.l[1];
+                int j1, p1;
+                level_pos(l1, (int)(row - plane * (((int64_t)1 << l1) + 1)), j1, p1);
+                out = s_rank[(P.nj + j1) * P.nb + P.T - m] + p1;
+                if (d > 2) {
+                    const int s = m + (j1 > 1 ? j1 : 1);
+                    out += s_out2[(int)(plane - ch.plane) * ch.nb2 + s - 2] << (j1 == 0 ? 1 : j1 - 1);
+                }
             }
             s_out[e] = out;
         }
         __syncthreads();
-        const double cg = P.scaled ? P.coeffs[lo] : 1.0;
-        const unsigned mag = magic_u32(n0);
-        int64_t idx[kScatterPer];
+        IDX idx[kScatterPer];
 #pragma unroll
         for (int r = 0; r < kScatterPer; ++r) {
-            const int64_t f = f0 + r * 256 + threadIdx.x;
+            const int o = r * 256 + threadIdx.x;
             idx[r] = -1;
-            if (f < f1) {
-                // t < kScatterChunk + n0; t n0 < 2^32 whenever n0 <= kScatterChunk,
-                // and a longer row leaves t / n0 in {0, 1}
-                const int t = (int)(f - ra * n0);
-                const int rr = n0 > kScatterChunk ? (t >= n0) : (int)__umulhi((unsigned)t, mag);
+            if (o < ch.npts) {
+                const int t = ch.t0 + o, rr = div_row(t, n0, ch.mag0);
                 int j0, p0;
                 level_pos(l0, t - rr * n0, j0, p0);
                 const int m = j0 > 1 ? j0 : 1;
-                idx[r] = point_pos(s_rank, P.nb, P.T, j0, p0, s_out[rr * nbud + m - 1]);
+                idx[r] = point_pos<IDX>(s_rank, P.nb, P.T, j0, p0, s_out[rr * nbud + m - 1]);
             }
         }
         double v[kScatterPer];
 #pragma unroll
         for (int r = 0; r < kScatterPer; ++r) v[r] = idx[r] >= 0 ? __ldg(P.sparse + idx[r]) : 0.0;
-        void *dst = P.ptrs[lo];
+        const double cg = P.scaled ? P.coeffs[ch.grid] : 1.0;
+        const int64_t f0 = ch.row * n0 + ch.t0;
+        if (P.fp64) {
+            double *dst = reinterpret_cast<double *>(P.ptrs[ch.grid]) + f0;
 #pragma unroll
-        for (int r = 0; r < kScatterPer; ++r) {
-            const int64_t f = f0 + r * 256 + threadIdx.x;
-            if (idx[r] >= 0) {
-                const double w = P.scaled ? cg * v[r] : v[r];
-                if (P.fp64) reinterpret_cast<double *>(dst)[f] = w;
-                else reinterpret_cast<float *>(dst)[f] = (float)w;
-            }
+            for (int r = 0; r < kScatterPer; ++r)
+                if (idx[r] >= 0) dst[r * 256 + threadIdx.x] = P.scaled ? cg * v[r] : v[r];
+        } else {
+            float *dst = reinterpret_cast<float *>(P.ptrs[ch.grid]) + f0;
+#pragma unroll
+            for (int r = 0; r < kScatterPer; ++r)
+                if (idx[r] >= 0) dst[r * 256 + threadIdx.x] = (float)(P.scaled ? cg * v[r] : v[r]);
         }
         __syncthreads();
     }
@@ -1451,10 +1509,11 @@ struct gbh_plan {
     int2 *d_chunks = nullptr;
     int nsub = 0, nchunks = 0;
     int64_t *d_rank = nullptr;        // scatter: subspace ranking table [d][n+1][n+d]
-    int64_t *d_scat_first = nullptr;  // scatter: first chunk of every grid [G+1]
+    ScatterChunk *d_scat = nullptr;   // scatter: chunk list
     int64_t nscat = 0;
     int rank_len = 0;
-    int scat_entries = 0;             // scatter: largest outer-part table of a chunk
+    int scat_ent = 0, scat_ent2 = 0;  // scatter: largest part tables of a chunk
+    bool scat_idx32 = false;          // scatter: sparse positions fit in 31 bits
     void **h_ptrs = nullptr;          // pinned staging for bind
     bool bound = false;
     int dev = 0;
@@ -1481,7 +1540,7 @@ void free_plan(gbh_plan *p)
     cudaFree(p->d_list);
     cudaFree(p->d_chunks);
     cudaFree(p->d_rank);
-    cudaFree(p->d_scat_first);
+    cudaFree(p->d_scat);
     if (p->h_ptrs) cudaFreeHost(p->h_ptrs);
     delete p;
 }
@@ -1662,14 +1721,18 @@ int build_sparse(gbh_plan *p)
     if (int e = upload(&p->d_list, list)) return e;
     const std::vector<int64_t> rank = build_rank(d, n);
     p->rank_len = (int)rank.size();
-    std::vector<int64_t> first(p->ngrids + 1, 0);
-    for (int g = 0; g < p->ngrids; ++g) {
-        first[g + 1] = first[g] + (p->info[g].N + kScatterChunk - 1) / kScatterChunk;
-        p->scat_entries = std::max(p->scat_entries, scatter_entries(p->info[g].l[0]));
-    }
-    p->nscat = first[p->ngrids];
+    std::vector<ScatterChunk> sch;
+    for (int g = 0; g < p->ngrids; ++g)
+        for (int64_t f0 = 0; f0 < p->info[g].N; f0 += kScatterChunk) {
+            sch.push_back(make_chunk(g, p->info[g].l, d, p->info[g].N, f0));
+            p->scat_ent = std::max(p->scat_ent, sch.back().nent);
+            p->scat_ent2 = std::max(p->scat_ent2, sch.back().nent2);
+        }
+    p->nscat = (int64_t)sch.size();
+    p->scat_idx32 = p->sparse_points < ((int64_t)1 << 31) &&
+                    *std::max_element(rank.begin(), rank.end()) < ((int64_t)1 << 31);
     if (int e = upload(&p->d_rank, rank)) return e;
-    if (int e = upload(&p->d_scat_first, first)) return e;
+    if (int e = upload(&p->d_scat, sch)) return e;
     return GBH_OK;
 }
 
@@ -1912,9 +1975,8 @@ int gbh_plan_scatter(gbh_plan *plan, const double *sparse, int scaled, void *str
     P.nb = P.T + 1;
     P.rank = plan->d_rank;
     P.rank_len = plan->rank_len;
-    P.max_entries = plan->scat_entries;
-    P.chunk_first = plan->d_scat_first;
-    P.ngrids = plan->ngrids;
+    P.max_ent = plan->scat_ent;
+    P.chunks = plan->d_scat;
     P.nchunks = plan->nscat;
     P.grids = plan->d_info;
     P.ptrs = plan->d_ptrs;
@@ -1922,13 +1984,15 @@ int gbh_plan_scatter(gbh_plan *plan, const double *sparse, int scaled, void *str
     P.sparse = sparse;
     P.scaled = scaled != 0;
     P.fp64 = plan->dtype == GBH_F64;
-    const size_t smem = sizeof(int64_t) * ((size_t)plan->rank_len + plan->scat_entries);
+    auto kern = plan->scat_idx32 ? k_scatter<int> : k_scatter<int64_t>;
+    const size_t smem = (plan->scat_idx32 ? sizeof(int) : sizeof(int64_t)) *
+                        ((size_t)plan->rank_len + plan->scat_ent + plan->scat_ent2);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GBH_ECUDA;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(P.nchunks, (int64_t)num_sms() * 8));
     ProfScope ps("scatter", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * plan->sparse_points);
-    k_scatter<<<(int)grid, 256, smem, s>>>(P);
+    kern<<<(int)grid, 256, smem, s>>>(P);
     ps.done();
     count_launches(1);
     return check_launch();
@@ -1959,9 +2023,9 @@ int gbh_sparse_index_of_grid(int d, int n, const int32_t *levels, int64_t *out)
         int b = T - std::max(j0, 1);
         for (int k = 1; k < d; ++k) {
             const int i = (int)((f / S[k]) % (((int64_t)1 << levels[k]) + 1));
-            out_m += sparse_pos(k, levels[k], i, nj, nb, rank.data(), b, W);
+            out_m += sparse_pos<int64_t>(k, levels[k], i, nj, nb, rank.data(), b, W);
         }
-        out[f] = point_pos(rank.data(), nb, T, j0, p0, out_m);
+        out[f] = point_pos<int64_t>(rank.data(), nb, T, j0, p0, out_m);
     }
     return GBH_OK;
 }
