@@ -4,7 +4,9 @@ The grids of a scheme are independent (Sec. 2: the coarse parallelism of the
 combination technique), so ranks split them with no exchange until the
 gather: every rank hierarchizes its own grids, gathers them into a partial
 fp64 sparse vector (the coefficients of other ranks' grids set to 0), and one
-sum all-reduce of the sparse vector completes the combination.
+sum all-reduce of the sparse vector completes the combination.  The way back
+needs no exchange: every rank holds the whole sparse vector after the
+all-reduce and scatters it onto its own grids (then dehierarchizes them).
 """
 from __future__ import annotations
 
