@@ -165,6 +165,19 @@ typedef struct gbh_plan gbh_plan;
 int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out);
 
 /*
+ * Scheme plan over a subset of the scheme's grids, for one rank of a job that
+ * splits the grids over ranks (the coarse parallelism of the combination
+ * technique, Sec. 2).  owned: host array of n_owned >= 1 strictly increasing
+ * indexes into the enumeration of gbh_plan_create_scheme; the plan holds
+ * those grids (in that order) with their coefficients and the whole sparse
+ * grid.  Its gather sums only these grids (a partial sparse vector that a sum
+ * over ranks completes, equal to a full plan's gather with the other
+ * coefficients set to 0); its scatter and execute touch only these grids.
+ * GBH_EINVAL for an empty, unordered or out-of-range list.
+ */
+int gbh_plan_create_scheme_subset(int d, int n, int dtype, int n_owned, const int32_t *owned, gbh_plan **out);
+
+/*
  * Plan for an arbitrary list of grids: levels is a host array [n_grids][d],
  * d in [1, 8], every level in [0, 17] (GBH_ERANGE otherwise).  Coefficients
  * are 1; gbh_plan_gather needs a plan made by gbh_plan_create_scheme.

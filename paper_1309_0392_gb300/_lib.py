@@ -50,6 +50,8 @@ _SIGS = {
     "gbh_tile_plan": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int, _I32P]),
     "gbh_plan_create_scheme": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(_VP)]),
+    "gbh_plan_create_scheme_subset": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     _I32P, ctypes.POINTER(_VP)]),
     "gbh_plan_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P, ctypes.c_int,
                                        ctypes.POINTER(_VP)]),
     "gbh_plan_destroy": (ctypes.c_int, [_VP]),

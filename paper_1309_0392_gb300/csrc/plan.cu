@@ -1778,11 +1778,17 @@ extern "C" {
 
 int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out)
 {
+    return gbh_plan_create_scheme_subset(d, n, dtype, -1, nullptr, out);
+}
+
+int gbh_plan_create_scheme_subset(int d, int n, int dtype, int n_owned, const int32_t *owned, gbh_plan **out)
+{
     if (!out) return GBH_EINVAL;
     *out = nullptr;
     if (d < 1 || d > kPlanMaxD || n < 1) return GBH_EINVAL;
     if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
     if (n + d - 1 > 30 + d - 1) return GBH_ERANGE;
+    if (n_owned >= 0 && (n_owned < 1 || !owned)) return GBH_EINVAL;
     gbh_plan *p = new (std::nothrow) gbh_plan();
     if (!p) return GBH_ENOMEM;
     p->d = d;
@@ -1795,6 +1801,20 @@ int gbh_plan_create_scheme(int d, int n, int dtype, gbh_plan **out)
         if (s < d) continue;
         const double c = ((q & 1) ? -1.0 : 1.0) * binom(d - 1, q);
         add_compositions(p, s, c);
+    }
+    if (n_owned >= 0) {
+        // keep the listed grids (strictly increasing scheme indexes)
+        const int all = (int)p->coeffs.size();
+        std::vector<int32_t> lv;
+        std::vector<double> cf;
+        for (int i = 0; i < n_owned; ++i) {
+            const int g = owned[i];
+            if (g < 0 || g >= all || (i > 0 && g <= owned[i - 1])) { delete p; return GBH_EINVAL; }
+            lv.insert(lv.end(), p->levels.begin() + (size_t)g * d, p->levels.begin() + (size_t)(g + 1) * d);
+            cf.push_back(p->coeffs[g]);
+        }
+        p->levels.swap(lv);
+        p->coeffs.swap(cf);
     }
     p->ngrids = (int)p->coeffs.size();
     int e = finish_plan(p);

@@ -20,10 +20,18 @@ class Plan:
         self._bound = None
 
     @classmethod
-    def scheme(cls, d: int, n: int, dtype="float64"):
+    def scheme(cls, d: int, n: int, dtype="float64", owned=None):
+        """Plan of the combination scheme (d, n); with `owned` (increasing
+        indexes into the scheme's enumeration) only those grids, for one rank
+        of a sharded job."""
         code = _lib.GBH_F64 if str(dtype).endswith("float64") else _lib.GBH_F32
         h = ctypes.c_void_p()
-        _lib.check(_lib.lib().gbh_plan_create_scheme(d, n, code, ctypes.byref(h)), "gbh_plan_create_scheme")
+        if owned is None:
+            _lib.check(_lib.lib().gbh_plan_create_scheme(d, n, code, ctypes.byref(h)), "gbh_plan_create_scheme")
+        else:
+            own = [int(g) for g in owned]
+            _lib.check(_lib.lib().gbh_plan_create_scheme_subset(d, n, code, len(own), _lib.levels_arg(own),
+                                                                ctypes.byref(h)), "gbh_plan_create_scheme_subset")
         return cls(h, d, code)
 
     @classmethod

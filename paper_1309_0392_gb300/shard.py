@@ -7,6 +7,7 @@ fp64 sparse vector (the coefficients of other ranks' grids set to 0), and one
 sum all-reduce of the sparse vector completes the combination.  The way back
 needs no exchange: every rank holds the whole sparse vector after the
 all-reduce and scatters it onto its own grids (then dehierarchizes them).
+On the GPU a rank's plan holds only its grids: Plan.scheme(d, n, owned=...).
 """
 from __future__ import annotations
 

@@ -222,6 +222,53 @@ def test_scatter_full_scheme_d4_n14():
     assert torch.equal(back, sparse)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_subset_plans_of_two_ranks(dtype):
+    """Plans over each rank's share of the grids: partial gathers are bit-exact
+    against the oracle with the other coefficients 0 and sum to the full
+    gather; scatter and execute touch only the rank's grids."""
+    from paper_1309_0392_gb300 import shard
+    d, n = 3, 5
+    lv, c = oracle.scheme(d, n)
+    parts = shard.partition_grids([oracle.num_points(l) for l in lv], 2)
+    host = [inputs.scheme_grid(l, 1000 + g) for g, l in enumerate(lv)]
+    if dtype == torch.float32:
+        host = [h.astype(np.float32).astype(np.float64) for h in host]
+    alphas = [oracle.hierarchize(h, l) for h, l in zip(host, lv)]
+    total = np.zeros(oracle.sparse_num_points(d, n))
+    for own in parts:
+        plan = gbh.Plan.scheme(d, n, dtype=str(dtype), owned=own)
+        assert np.array_equal(plan.levels(), lv[own]) and np.array_equal(plan.coeffs(), c[own])
+        grids = [torch.tensor(host[g], dtype=dtype, device="cuda") for g in own]
+        plan.bind(grids)
+        plan.execute(gbh.GBH_HIERARCHIZE)
+        tol = 1e-13 if dtype == torch.float64 else 1e-5
+        for t, g in zip(grids, own):
+            assert rel_err(t.cpu().double().numpy(), alphas[g], host[g]) <= tol * 4
+        if dtype == torch.float64:
+            exact = [torch.tensor(alphas[g], device="cuda") for g in own]
+            plan.bind(exact)
+        sparse = torch.empty(plan.sparse_points, dtype=torch.float64, device="cuda")
+        plan.gather(sparse)
+        if dtype == torch.float64:
+            assert np.array_equal(sparse.cpu().numpy(), oracle.gather(d, n, lv, shard.owned_coeffs(c, own), alphas))
+        total += sparse.cpu().numpy()
+        s = np.random.default_rng(33).uniform(-1, 1, plan.sparse_points)
+        plan.scatter(torch.tensor(s, device="cuda"))
+        back = oracle.scatter(d, n, lv[own], c[own], s)
+        for t, r in zip(plan._bound, back):
+            want = r if dtype == torch.float64 else r.astype(np.float32)
+            assert np.array_equal(t.cpu().numpy(), want)
+    full = oracle.gather(d, n, lv, c, alphas)
+    assert np.abs(total - full).max() <= (1e-14 if dtype == torch.float64 else 1e-5) * np.abs(full).max() * 8
+
+
+def test_subset_plan_rejects_bad_lists():
+    for owned in ([], [3, 1], [0, 0], [-1], [10 ** 6]):
+        with pytest.raises(gbh.GbhError):
+            gbh.Plan.scheme(3, 4, owned=owned)
+
+
 def test_scatter_argument_errors():
     plan = gbh.Plan.scheme(2, 4)
     sparse = torch.zeros(plan.sparse_points, dtype=torch.float64, device="cuda")
