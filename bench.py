@@ -256,6 +256,15 @@ def forms(args, dev, hbm):
         measure(f"adjoint_{nm}_16x_8_8_8", t, lv5, gbh.GBH_ADJOINT, 5, es, batch=16)
         measure(f"fwd_{nm}_16x_8_8_8", t, lv5, gbh.GBH_HIERARCHIZE, 5, es, batch=16)
         del t
+    # the paper's dimension-0-heavy shapes: one pole of level 27, and ten
+    # dimensions with dimension 0 long and every other one 3 points
+    for name, lv in (("1d_27", (27,)), ("10d_12_1x9", (12,) + (1,) * 9)):
+        t = torch.empty(inputs.num_points(lv), dtype=torch.float64, device=dev).uniform_(-1, 1)
+        measure(f"fwd_fp64_{name}", t, lv, gbh.GBH_HIERARCHIZE, 5, 8,
+                restore=lambda: gbh.transform(t, lv, gbh.GBH_DEHIERARCHIZE))
+        measure(f"dehier_fp64_{name}", t, lv, gbh.GBH_DEHIERARCHIZE, 5, 8,
+                restore=lambda: gbh.transform(t, lv, gbh.GBH_HIERARCHIZE))
+        del t
     torch.cuda.empty_cache()
     out.update(scheme_forms(dev, hbm))
     out.update(autograd_forms(dev, hbm))

@@ -225,9 +225,13 @@ __device__ __forceinline__ double g_from_fixed_fast(long long v, long long Xhi)
     return __longlong_as_double(v == 0 ? 0ll : b + Xhi);
 }
 
+// ROWS: poles are rows of n contiguous elements, row r starting at r * rs
+// (rs = n for the rows of dimension 0; rs = n - 1 for the dyadic blocks of a
+// long pole, which share their end points).  Otherwise pole t is the pole
+// (t / S, t % S) of a dimension with stride S.
 template <typename T, int OP, bool FIX, bool ROWS>
 __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S, int64_t poles, int l, int G,
-                                                    int g0)
+                                                    int g0, int64_t rs)
 {
     using V = typename std::conditional<FIX, long long, T>::type;
     extern __shared__ __align__(16) unsigned char smr[];
@@ -253,8 +257,9 @@ __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S
     auto locate = [&](int w, int &sidx, int &i) -> int64_t {
         if (ROWS) {
             sidx = w;
-            i = w - (int)__umulhi((unsigned)w, magN) * n;
-            return t0 * n + w;
+            const int r = (int)__umulhi((unsigned)w, magN);
+            i = w - r * n;
+            return (t0 + r) * rs + i;
         }
         i = magG ? (int)__umulhi((unsigned)w, magG) : w;
         const int g = w - i * Gc;
@@ -407,12 +412,12 @@ int sweep_level(T *u, const Geom &g, int k, cudaStream_t st)
     return GBH_OK;
 }
 
+// poles of level l: rows at stride rs (ROWS), else the poles of a dimension
+// of stride S; `bytes` is the launch's algorithmic traffic
 template <typename T, int OP, bool FIX, bool ROWS>
-int launch_group(T *u, const Geom &g, int k, cudaStream_t st)
+int launch_group_raw(T *u, int64_t S, int64_t rs, int64_t poles, int l, double bytes, cudaStream_t st)
 {
-    const int l = g.l[k];
-    const int n = (int)g.n[k];
-    const int64_t poles = g.total / g.n[k];
+    const int n = (1 << l) + 1;
     const int G = std::max(1, kGroupElems / n);
     const int64_t blocks = (poles + G - 1) / G;
     if (blocks > INT32_MAX) return GBH_ERANGE;
@@ -428,11 +433,44 @@ int launch_group(T *u, const Geom &g, int k, cudaStream_t st)
     // D grows by at most l + 1 (hat weights along a pole sum to at most l + 1);
     // A sums at most 2 l children besides the doubled point
     const int g0 = OP == OP_H ? 59 : 59 - (int)std::ceil(std::log2((double)l + 1.0));
-    ProfScope ps(ROWS ? "plain_rows_group" : "plain_pole_group", st, 2.0 * sizeof(T) * (double)g.total);
-    k_pole_group<T, OP, FIX, ROWS><<<(unsigned)blocks, 256, smem, st>>>(u, g.S[k], poles, l, G, g0);
+    ProfScope ps(ROWS ? "plain_rows_group" : "plain_pole_group", st, bytes);
+    k_pole_group<T, OP, FIX, ROWS><<<(unsigned)blocks, 256, smem, st>>>(u, S, poles, l, G, g0, rs);
     ps.done();
     count_launches(1);
     return check_launch();
+}
+
+template <typename T, int OP, bool FIX, bool ROWS>
+int launch_group(T *u, const Geom &g, int k, cudaStream_t st)
+{
+    return launch_group_raw<T, OP, FIX, ROWS>(u, g.S[k], g.n[k], g.total / g.n[k], g.l[k],
+                                              2.0 * sizeof(T) * (double)g.total, st);
+}
+
+// One long pole (a single grid of one dimension, level 14 < L <= 28) by the
+// dyadic split of its index set: with blocks of level m, the points that are
+// not multiples of 2^m have both predecessors inside their block
+// [a 2^m, (a+1) 2^m], so hierarchization is a level-m transform of every
+// block (end points read, never written) followed by a level L-m transform
+// of the coarse pole of the multiples of 2^m, which reads only those.  The
+// inverse runs the two parts in the opposite order.  Each transform keeps
+// the per-point operation of Alg. 1, so results equal the per-level sweep.
+template <typename T, int OP, bool FIX>
+int long_pole_split(T *u, int L, cudaStream_t st)
+{
+    const int m = std::max(13, L - 14);
+    const int64_t bm = (int64_t)1 << m, blocks = (int64_t)1 << (L - m);
+    const double bytes = 2.0 * sizeof(T) * (double)(((int64_t)1 << L) + 1);
+    auto fine = [&] { return launch_group_raw<T, OP, FIX, true>(u, 1, bm, blocks, m, bytes, st); };
+    auto coarse = [&] {
+        return launch_group_raw<T, OP, FIX, false>(u, bm, 0, 1, L - m, 2.0 * sizeof(T) * (double)(blocks + 1), st);
+    };
+    if (OP == OP_H) {
+        if (int e = fine()) return e;
+        return coarse();
+    }
+    if (int e = coarse()) return e;
+    return fine();
 }
 
 template <typename T, int OP>
@@ -442,7 +480,11 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
     const int64_t poles = g.total / g.n[k];
     const bool fix = sizeof(T) == 8 && fixed;
     if (k == 0) {
-        if (g.n[0] > kGroupMaxElems) return sweep_level<T, OP>(u, g, 0, st);
+        if (g.n[0] > kGroupMaxElems) {
+            if (OP != OP_A && g.d == 1 && g.batch == 1 && l <= 28)
+                return fix ? long_pole_split<T, OP, sizeof(T) == 8>(u, l, st) : long_pole_split<T, OP, false>(u, l, st);
+            return sweep_level<T, OP>(u, g, 0, st);
+        }
         return fix ? launch_group<T, OP, sizeof(T) == 8, true>(u, g, 0, st) : launch_group<T, OP, false, true>(u, g, 0, st);
     }
     if (fix && g.n[k] <= kGroupElems) return launch_group<T, OP, sizeof(T) == 8, false>(u, g, k, st);

@@ -150,6 +150,30 @@ def test_long_poles(levels, op):
     assert rel_err(run(u, levels, op), ORACLE[op](u, levels), u) <= TOL64
 
 
+@pytest.mark.parametrize("levels", [(27,), (12,) + (1,) * 9, (1,) * 9 + (12,)])
+@pytest.mark.parametrize("op", ["h", "d", "a"])
+def test_dim0_heavy_shapes(levels, op):
+    """The paper's extreme shapes (Sec. 4): one pole of level 27 (134 M points),
+    and ten dimensions with one long dimension and 3 points in every other;
+    bit-exact on the plain path, within the tolerance on the default path."""
+    u = inputs.uniform(levels, 9)
+    ref = ORACLE[op](u, levels)
+    assert np.array_equal(run(u, levels, op, path=gbh.GBH_PATH_PLAIN), ref)
+    assert rel_err(run(u, levels, op), ref, u) <= TOL64
+
+
+@pytest.mark.parametrize("levels", [(28,), (20,)])
+@pytest.mark.parametrize("op", ["h", "d"])
+def test_long_pole_split(levels, op):
+    """A single long pole splits into dyadic blocks of level max(13, L - 14)
+    and their coarse pole (the largest blocks at level 28); the split keeps
+    the serial operation order, so the plain path stays bit-exact."""
+    u = inputs.uniform(levels, 11)
+    ref = ORACLE[op](u, levels)
+    assert np.array_equal(run(u, levels, op, path=gbh.GBH_PATH_PLAIN), ref)
+    assert rel_err(run(u, levels, op), ref, u) <= TOL64
+
+
 @pytest.mark.parametrize("op", ["h", "d", "a"])
 def test_same_shape_batch(op):
     levels, B = (4, 3, 5), 5
