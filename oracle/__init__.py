@@ -46,7 +46,8 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_num_points.restype = _I64
             lib.orc_num_points.argtypes = [ctypes.c_int, _IP]
-            for name in ("orc_hierarchize", "orc_dehierarchize", "orc_hierarchize_adjoint"):
+            for name in ("orc_hierarchize", "orc_dehierarchize", "orc_hierarchize_adjoint",
+                         "orc_dehierarchize_adjoint"):
                 f = getattr(lib, name)
                 f.restype = None
                 f.argtypes = [_DP, ctypes.c_int, _IP]
@@ -120,6 +121,11 @@ def dehierarchize(a, levels):
 def hierarchize_adjoint(y, levels):
     """Exact transpose of :func:`hierarchize` on a copy of ``y``."""
     return _transform("orc_hierarchize_adjoint", y, levels)
+
+
+def dehierarchize_adjoint(y, levels):
+    """Exact transpose of :func:`dehierarchize` on a copy of ``y``."""
+    return _transform("orc_dehierarchize_adjoint", y, levels)
 
 
 def _at(name, u, levels, flat_indices):

@@ -32,6 +32,8 @@
  *     u[i] = a[i] + 0.5 * (u[left] + u[right]).
  *   - The adjoint is the exact transpose: coarse to fine, each point scatters
  *     -0.5 times its own (still original) value into both predecessors.
+ *   - The transpose of the dehierarchization runs fine to coarse: each point
+ *     adds 0.5 times its accumulated value to both predecessors.
  *   - Combination scheme (Sec. 2, "The Combination Technique"): level vectors
  *     with l_k >= 1 and |l|_1 = n + d - 1 - q, q = 0..d-1, coefficient
  *     (-1)^q C(d-1, q); enumerated by q ascending, then lexicographically
@@ -124,6 +126,21 @@ static void pole_adjoint(double *y, int64_t S, int l)
     }
 }
 
+/* Transpose of pole_dehierarchize (the inverse read backwards): levels l down
+ * to 1; every point of a level adds half of its value, which already holds
+ * the contributions of all finer points, to both predecessors. */
+static void pole_dehierarchize_adjoint(double *y, int64_t S, int l)
+{
+    const int64_t last = (int64_t)1 << l;
+    for (int lev = l; lev >= 1; --lev) {
+        const int64_t s = (int64_t)1 << (l - lev);
+        for (int64_t i = s; i < last; i += 2 * s) {
+            y[(i - s) * S] = y[(i - s) * S] + 0.5 * y[i * S];
+            y[(i + s) * S] = y[(i + s) * S] + 0.5 * y[i * S];
+        }
+    }
+}
+
 typedef void (*pole_fn)(double *, int64_t, int);
 
 /* Outer two loops of Alg. 1: for each dimension, for every 1-D pole in it. */
@@ -156,6 +173,14 @@ void orc_dehierarchize(double *u, int d, const int *levels)
 void orc_hierarchize_adjoint(double *u, int d, const int *levels)
 {
     sweep_all_dims(u, d, levels, pole_adjoint);
+}
+
+/* Exact transpose of orc_dehierarchize (the inverse of the transpose of
+ * orc_hierarchize), in place: differentiates through the dehierarchization
+ * that follows the scatter of the iterated combination technique (Sec. 2). */
+void orc_dehierarchize_adjoint(double *u, int d, const int *levels)
+{
+    sweep_all_dims(u, d, levels, pole_dehierarchize_adjoint);
 }
 
 /* ------------------------------------------------------------------------ */

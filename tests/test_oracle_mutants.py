@@ -1,7 +1,7 @@
 """Planted mistakes in the oracle: each mutant of gbh_oracle.c (a flipped sign,
 a shifted index, a wrong loop bound or order, a wrong stride) is compiled on
 the CPU and must fail at least one of the independent pins (hat-basis brute
-force, round trip, dot product; for the sparse grid, the coordinate
+force against Phi, Phi^-1 and their transposes; for the sparse grid, the coordinate
 dictionary and the transpose identity).  Shows that the pins can catch a
 plausible error anywhere in the sweeps, the gather and the scatter.  CPU only."""
 import ctypes
@@ -31,6 +31,10 @@ MUTANTS = {
     "adjoint_one_parent": ("            y[(i + s) * S] = y[(i + s) * S] - 0.5 * y[i * S];",
                            "            y[(i - s) * S] = y[(i - s) * S] - 0.5 * y[i * S];"),
     "stride_off_by_one": ("for (int m = 0; m < k && m < d; ++m)", "for (int m = 0; m <= k && m < d; ++m)"),
+    "dehier_adjoint_wrong_order": ("    for (int lev = l; lev >= 1; --lev) {\n        const int64_t s = (int64_t)1 << (l - lev);\n        for (int64_t i = s; i < last; i += 2 * s) {\n            y[(i - s) * S] = y[(i - s) * S] + 0.5",
+                                   "    for (int lev = 1; lev <= l; ++lev) {\n        const int64_t s = (int64_t)1 << (l - lev);\n        for (int64_t i = s; i < last; i += 2 * s) {\n            y[(i - s) * S] = y[(i - s) * S] + 0.5"),
+    "dehier_adjoint_sign": ("            y[(i + s) * S] = y[(i + s) * S] + 0.5 * y[i * S];",
+                            "            y[(i + s) * S] = y[(i + s) * S] - 0.5 * y[i * S];"),
 }
 
 # mistakes in the sparse-grid index, the gather and the scatter (every mutant
@@ -58,7 +62,7 @@ def _compile(tmp_path, name, old, new):
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                            str(path), "-o", str(so), "-lm"])
     lib = ctypes.CDLL(str(so))
-    for fn in ("orc_hierarchize", "orc_dehierarchize", "orc_hierarchize_adjoint"):
+    for fn in ("orc_hierarchize", "orc_dehierarchize", "orc_hierarchize_adjoint", "orc_dehierarchize_adjoint"):
         getattr(lib, fn).argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int)]
     return lib
@@ -82,6 +86,8 @@ def _pins_hold(lib):
         if np.abs(_run(lib, "orc_dehierarchize", u, levels) - phi @ u).max() > 1e-12:
             return False
         if np.abs(_run(lib, "orc_hierarchize_adjoint", u, levels) - np.linalg.solve(phi.T, u)).max() > 1e-12:
+            return False
+        if np.abs(_run(lib, "orc_dehierarchize_adjoint", u, levels) - phi.T @ u).max() > 1e-12 * np.abs(phi.T @ u).max():
             return False
     return True
 

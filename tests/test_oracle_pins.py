@@ -56,6 +56,8 @@ def test_brute_force_hat_basis(orc, levels):
     # the transpose of Phi^{-1}
     y = rng.uniform(-1, 1, phi.shape[0])
     assert np.abs(orc.hierarchize_adjoint(y, levels) - np.linalg.solve(phi.T, y)).max() <= 1e-12
+    # the transpose of Phi
+    assert np.abs(orc.dehierarchize_adjoint(y, levels) - phi.T @ y).max() <= 1e-12 * np.abs(phi.T @ y).max()
 
 
 @pytest.mark.parametrize("levels", LEVELS_SMALL)
@@ -150,6 +152,37 @@ def test_adjoint_dot_product(orc, levels):
     hx = orc.hierarchize(x, levels)
     lhs, rhs = hx @ y, x @ orc.hierarchize_adjoint(y, levels)
     assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(hx) * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("levels", [(6,), (4, 3), (3, 3, 3), (2, 2, 1, 2)])
+def test_dehierarchize_adjoint_dot_product_and_inverse(orc, levels):
+    """<D x, y> = <x, D^T y>, and D^T inverts the transpose of hierarchization
+    (D^T H^T = (H D)^T = I)."""
+    rng = np.random.default_rng(10)
+    x = rng.uniform(-1, 1, orc.num_points(levels))
+    y = rng.uniform(-1, 1, orc.num_points(levels))
+    dx = orc.dehierarchize(x, levels)
+    dty = orc.dehierarchize_adjoint(y, levels)
+    assert abs(dx @ y - x @ dty) <= 1e-12 * np.linalg.norm(dx) * np.linalg.norm(y)
+    assert np.abs(orc.dehierarchize_adjoint(orc.hierarchize_adjoint(y, levels), levels) - y).max() <= 1e-13
+    assert np.abs(orc.hierarchize_adjoint(dty, levels) - y).max() <= 1e-13 * np.abs(dty).max()
+
+
+def test_dehierarchize_adjoint_1d_closed_form(orc):
+    """One pole: (D^T y)[p] = sum_i phi_p(x_i) y_i, so with y = 1 the value at
+    p is the sum of its hat over the nodes: 2^l / 2^{level(p)} for an interior
+    p, (2^l + 1) / 2 at either boundary point (exact, dyadic)."""
+    l = 6
+    n = 2 ** l + 1
+    got = orc.dehierarchize_adjoint(np.ones(n), (l,))
+    want = np.empty(n)
+    for p in range(n):
+        if p in (0, n - 1):
+            want[p] = (2 ** l + 1) / 2
+        else:
+            tz = (p & -p).bit_length() - 1
+            want[p] = 2.0 ** tz          # hat of half-width 2^tz nodes sums to 2^tz
+    assert np.array_equal(got, want)
 
 
 @pytest.mark.parametrize("levels", [(3, 4), (2, 3, 2)])
