@@ -56,7 +56,8 @@ typedef enum {
 typedef enum {
     GBH_HIERARCHIZE = 0,    /* nodal -> hierarchical (Alg. 1)                    */
     GBH_DEHIERARCHIZE = 1,  /* hierarchical -> nodal (inverse of Alg. 1)         */
-    GBH_ADJOINT = 2         /* transpose of Alg. 1                               */
+    GBH_ADJOINT = 2,        /* transpose of Alg. 1                               */
+    GBH_DEHIERARCHIZE_ADJOINT = 3  /* transpose of the inverse (plain path only)  */
 } gbh_op;
 
 /* ------------------------------------------------------------------------ */
@@ -91,6 +92,18 @@ int gbh_dehierarchize(void *data, int d, const int32_t *levels, int dtype, void 
  * hierarchical predecessor p is).  Arguments as for gbh_hierarchize.
  */
 int gbh_hierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype, void *stream);
+
+/*
+ * Transpose of gbh_dehierarchize, in place: per pole, fine to coarse, every
+ * interior point adds half of its accumulated value to both hierarchical
+ * predecessors (boundary points change too).  It is the inverse of
+ * gbh_hierarchize_adjoint, and the backward step through the
+ * dehierarchization that follows the scatter of the iterated combination
+ * technique (Sec. 2).  Computed on the per-dimension path in native
+ * arithmetic, in the serial operation order (fp64 bit-identical to a serial
+ * run).  Arguments as for gbh_hierarchize.
+ */
+int gbh_dehierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype, void *stream);
 
 /* Execution path of gbh_transform. */
 typedef enum {
@@ -209,7 +222,7 @@ int gbh_plan_bind(gbh_plan *plan, void *const *grid_ptrs, void *stream);
 
 /*
  * Transform every bound grid in place (op = GBH_HIERARCHIZE or
- * GBH_DEHIERARCHIZE; GBH_EUNSUPPORTED for the transpose) with one persistent
+ * GBH_DEHIERARCHIZE; GBH_EUNSUPPORTED for the transposes) with one persistent
  * kernel launch driven by a device work queue.  Each grid is transformed group
  * of dimensions by group of dimensions (consecutive dimensions whose pole sets
  * fit a shared-memory tile), fp64 in int64 fixed point per tile; results agree

@@ -11,12 +11,12 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import (GBH_ADJOINT, GBH_DEHIERARCHIZE, GBH_HIERARCHIZE, GBH_PATH_AUTO,  # noqa: F401
-                   GBH_PATH_FUSED, GBH_PATH_GROUPED, GBH_PATH_PLAIN, GBH_ARITH_AUTO, GBH_ARITH_NATIVE,
-                   GBH_ARITH_FIXED, GbhError, sparse_index_of_grid)
+from ._lib import (GBH_ADJOINT, GBH_DEHIERARCHIZE, GBH_DEHIERARCHIZE_ADJOINT, GBH_HIERARCHIZE,  # noqa: F401
+                   GBH_PATH_AUTO, GBH_PATH_FUSED, GBH_PATH_GROUPED, GBH_PATH_PLAIN, GBH_ARITH_AUTO,
+                   GBH_ARITH_NATIVE, GBH_ARITH_FIXED, GbhError, sparse_index_of_grid)
 
-__all__ = ["hierarchize", "dehierarchize", "hierarchize_adjoint", "transform", "num_points",
-           "Plan", "HierarchizeFn", "GbhError", "sparse_index_of_grid"]
+__all__ = ["hierarchize", "dehierarchize", "hierarchize_adjoint", "dehierarchize_adjoint", "transform", "num_points",
+           "Plan", "HierarchizeFn", "DehierarchizeFn", "GbhError", "sparse_index_of_grid"]
 
 
 def num_points(levels) -> int:
@@ -44,7 +44,7 @@ def _stream_ptr(t, stream):
 def transform(t, levels, op=GBH_HIERARCHIZE, *, path=GBH_PATH_AUTO, tile=None, arith=0,
               stream=None, batch=None):
     """In-place transform of grid tensor ``t`` (op: GBH_HIERARCHIZE,
-    GBH_DEHIERARCHIZE or GBH_ADJOINT).  With ``batch=B`` the tensor holds B
+    GBH_DEHIERARCHIZE, GBH_ADJOINT or GBH_DEHIERARCHIZE_ADJOINT).  With ``batch=B`` the tensor holds B
     grids of the level vector back to back.  Returns ``t``."""
     B = 1 if batch is None else int(batch)
     if B < 1:
@@ -98,5 +98,10 @@ def hierarchize_adjoint(t, levels, **kw):
     return transform(t, levels, GBH_ADJOINT, **kw)
 
 
+def dehierarchize_adjoint(t, levels, **kw):
+    """Transpose of :func:`dehierarchize` in place."""
+    return transform(t, levels, GBH_DEHIERARCHIZE_ADJOINT, **kw)
+
+
 from .plan import Plan  # noqa: E402
-from .autograd import HierarchizeFn  # noqa: E402
+from .autograd import DehierarchizeFn, HierarchizeFn  # noqa: E402

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libgbh.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "gbh.h")
 
 GBH_F32, GBH_F64 = 0, 1
-GBH_HIERARCHIZE, GBH_DEHIERARCHIZE, GBH_ADJOINT = 0, 1, 2
+GBH_HIERARCHIZE, GBH_DEHIERARCHIZE, GBH_ADJOINT, GBH_DEHIERARCHIZE_ADJOINT = 0, 1, 2, 3
 GBH_PATH_AUTO, GBH_PATH_PLAIN, GBH_PATH_FUSED, GBH_PATH_GROUPED = 0, 1, 2, 3
 GBH_ARITH_AUTO, GBH_ARITH_NATIVE, GBH_ARITH_FIXED = 0, 1, 2
 
@@ -42,6 +42,7 @@ _SIGS = {
     "gbh_hierarchize": (ctypes.c_int, [_VP, ctypes.c_int, _I32P, ctypes.c_int, _VP]),
     "gbh_dehierarchize": (ctypes.c_int, [_VP, ctypes.c_int, _I32P, ctypes.c_int, _VP]),
     "gbh_hierarchize_adjoint": (ctypes.c_int, [_VP, ctypes.c_int, _I32P, ctypes.c_int, _VP]),
+    "gbh_dehierarchize_adjoint": (ctypes.c_int, [_VP, ctypes.c_int, _I32P, ctypes.c_int, _VP]),
     "gbh_transform": (ctypes.c_int, [_VP, ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(Options), _VP]),
     "gbh_transform_batched": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, _I32P, ctypes.c_int,

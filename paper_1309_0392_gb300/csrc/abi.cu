@@ -152,7 +152,8 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
                           int op, const gbh_options *opt, void *stream)
 {
     if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
-    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE && op != GBH_ADJOINT) return GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE && op != GBH_ADJOINT && op != GBH_DEHIERARCHIZE_ADJOINT)
+        return GBH_EINVAL;
     if (!data) return GBH_EINVAL;
     const int es = dtype == GBH_F64 ? 8 : 4;
     if (reinterpret_cast<uintptr_t>(data) % es) return GBH_EALIGN;
@@ -192,6 +193,11 @@ int gbh_dehierarchize(void *data, int d, const int32_t *levels, int dtype, void 
 int gbh_hierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype, void *stream)
 {
     return gbh_transform(data, d, levels, dtype, GBH_ADJOINT, nullptr, stream);
+}
+
+int gbh_dehierarchize_adjoint(void *data, int d, const int32_t *levels, int dtype, void *stream)
+{
+    return gbh_transform(data, d, levels, dtype, GBH_DEHIERARCHIZE_ADJOINT, nullptr, stream);
 }
 
 const char *gbh_status_string(int status)

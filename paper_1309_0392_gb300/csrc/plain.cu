@@ -23,14 +23,15 @@
 namespace gbh {
 namespace {
 
-enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE, OP_A = GBH_ADJOINT };
+enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE, OP_A = GBH_ADJOINT, OP_DT = GBH_DEHIERARCHIZE_ADJOINT };
 
 constexpr int kRegPoleMaxLevel = 5;      // poles up to 33 points kept in registers (65 for fp32)
 constexpr int64_t kMinPolesForThreadPerPole = 152 * 64;
 
 // ---------------------------------------------------------------------------
 // 1-D pole transforms; the loop order is that of Alg. 1 (fine to coarse) for
-// hierarchization, coarse to fine for the inverse and the transpose.
+// hierarchization, coarse to fine for the inverse and the transpose, fine to
+// coarse for the transpose of the inverse.
 // ---------------------------------------------------------------------------
 
 template <typename T, int OP, int L>
@@ -51,7 +52,7 @@ __device__ __forceinline__ void transform_regs(T *v)
 #pragma unroll
             for (int i = s; i < last; i += 2 * s) v[i] = v[i] + T(0.5) * (v[i - s] + v[i + s]);
         }
-    } else {
+    } else if (OP == OP_A) {
 #pragma unroll
         for (int lev = 1; lev <= L; ++lev) {
             const int s = 1 << (L - lev);
@@ -59,6 +60,16 @@ __device__ __forceinline__ void transform_regs(T *v)
             for (int i = s; i < last; i += 2 * s) {
                 v[i - s] = v[i - s] - T(0.5) * v[i];
                 v[i + s] = v[i + s] - T(0.5) * v[i];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int lev = L; lev >= 1; --lev) {
+            const int s = 1 << (L - lev);
+#pragma unroll
+            for (int i = s; i < last; i += 2 * s) {
+                v[i - s] = v[i - s] + T(0.5) * v[i];
+                v[i + s] = v[i + s] + T(0.5) * v[i];
             }
         }
     }
@@ -80,13 +91,22 @@ __device__ __forceinline__ void transform_global(T *__restrict__ p, int64_t S, i
             for (int64_t i = s; i < last; i += 2 * s)
                 p[i * S] = p[i * S] + T(0.5) * (p[(i - s) * S] + p[(i + s) * S]);
         }
-    } else {
+    } else if (OP == OP_A) {
         for (int lev = 1; lev <= l; ++lev) {
             const int64_t s = (int64_t)1 << (l - lev);
             for (int64_t i = s; i < last; i += 2 * s) {
                 const T v = p[i * S];
                 p[(i - s) * S] = p[(i - s) * S] - T(0.5) * v;
                 p[(i + s) * S] = p[(i + s) * S] - T(0.5) * v;
+            }
+        }
+    } else {
+        for (int lev = l; lev >= 1; --lev) {
+            const int64_t s = (int64_t)1 << (l - lev);
+            for (int64_t i = s; i < last; i += 2 * s) {
+                const T v = p[i * S];
+                p[(i - s) * S] = p[(i - s) * S] + T(0.5) * v;
+                p[(i + s) * S] = p[(i + s) * S] + T(0.5) * v;
             }
         }
     }
@@ -110,7 +130,7 @@ __global__ void __launch_bounds__(256) k_pole_regs(T *__restrict__ u, int64_t S,
         transform_regs<T, OP, L>(v);
 #pragma unroll
         for (int i = 0; i < n; ++i)
-            if (OP == OP_A || (i > 0 && i < n - 1)) p[i * S] = v[i];
+            if (OP == OP_A || OP == OP_DT || (i > 0 && i < n - 1)) p[i * S] = v[i];
     }
 }
 
@@ -130,13 +150,14 @@ __global__ void __launch_bounds__(256) k_pole_global(T *__restrict__ u, int64_t 
 // ---------------------------------------------------------------------------
 
 // H / D: the level-lev points i = (2q+1) s of every pole.
-// Adjoint: the points p = 2 s q that receive from level-lev children p -/+ s.
+// Transposes: the points p = 2 s q that receive from level-lev children
+// p -/+ s (left, then right: the order of the serial scatter).
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_level(T *__restrict__ u, int64_t S, int64_t n, int64_t outer,
                                                int l, int lev)
 {
     const int64_t s = (int64_t)1 << (l - lev);
-    const int64_t per = (OP == OP_A) ? (((int64_t)1 << (lev - 1)) + 1) : ((int64_t)1 << (lev - 1));
+    const int64_t per = (OP == OP_A || OP == OP_DT) ? (((int64_t)1 << (lev - 1)) + 1) : ((int64_t)1 << (lev - 1));
     const int64_t items = outer * S * per;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < items;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -144,11 +165,12 @@ __global__ void __launch_bounds__(256) k_level(T *__restrict__ u, int64_t S, int
         const int64_t rest = w / S;
         const int64_t q = rest % per, o = rest / per;
         T *p = u + o * S * n + j;
-        if (OP == OP_A) {
+        if (OP == OP_A || OP == OP_DT) {
             const int64_t i = 2 * s * q;
+            const T h = OP == OP_A ? T(-0.5) : T(0.5);
             T y = p[i * S];
-            if (q > 0) y = y - T(0.5) * p[(i - s) * S];
-            if (q < per - 1) y = y - T(0.5) * p[(i + s) * S];
+            if (q > 0) y = y + h * p[(i - s) * S];
+            if (q < per - 1) y = y + h * p[(i + s) * S];
             p[i * S] = y;
         } else {
             const int64_t i = (2 * q + 1) * s;
@@ -324,6 +346,27 @@ __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S
             if (i == 0 || i == last) continue;
             put(a, sv[sidx]);
         }
+    } else if (OP == OP_DT) {
+        // level by level, fine to coarse: the parents p = 2 s q of level-lev
+        // children take half of each child's value (left, then right); a
+        // child's value is final once every finer level has been gathered
+        for (int lev = l; lev >= 1; --lev) {
+            const int s = 1 << (l - lev), per = (1 << (lev - 1)) + 1;
+            for (int w = threadIdx.x; w < Gc * per; w += blockDim.x) {
+                const int r = w / per, q = w - r * per, p = 2 * s * q;
+                V *row = sv + r * n;
+                V y = row[p];
+                if (q > 0) y = y + V(0.5) * row[p - s];
+                if (q < per - 1) y = y + V(0.5) * row[p + s];
+                row[p] = y;
+            }
+            __syncthreads();
+        }
+        for (int w = threadIdx.x; w < cnt; w += blockDim.x) {
+            int sidx, i;
+            const int64_t a = locate(w, sidx, i);
+            put(a, sv[sidx]);
+        }
     } else if constexpr (FIX) {
         // every point at once from the staged values (exact):
         // 2 y[p] = 2 x[p] - sum_{t < lowbit(p)} (x[p - t] + x[p + t])
@@ -392,6 +435,15 @@ int sweep_level(T *u, const Geom &g, int k, cudaStream_t st)
     if (OP == OP_H) {
         for (int lev = l; lev >= 1; --lev) {
             const int64_t items = outer * g.S[k] * ((int64_t)1 << (lev - 1));
+            ProfScope ps("plain_level", st, 2.0 * sizeof(T) * (double)items);
+            k_level<T, OP><<<grid_for(items, 256), 256, 0, st>>>(u, g.S[k], g.n[k], outer, l, lev);
+            ps.done();
+            count_launches(1);
+            if (int e = check_launch()) return e;
+        }
+    } else if (OP == OP_DT) {
+        for (int lev = l; lev >= 1; --lev) {
+            const int64_t items = outer * g.S[k] * (((int64_t)1 << (lev - 1)) + 1);
             ProfScope ps("plain_level", st, 2.0 * sizeof(T) * (double)items);
             k_level<T, OP><<<grid_for(items, 256), 256, 0, st>>>(u, g.S[k], g.n[k], outer, l, lev);
             ps.done();
@@ -478,16 +530,18 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
 {
     const int l = g.l[k];
     const int64_t poles = g.total / g.n[k];
-    const bool fix = sizeof(T) == 8 && fixed;
+    // fp64 may compute in fixed point; the transpose of D runs natively
+    constexpr bool kFixable = sizeof(T) == 8 && OP != OP_DT;
+    const bool fix = kFixable && fixed;
     if (k == 0) {
         if (g.n[0] > kGroupMaxElems) {
-            if (OP != OP_A && g.d == 1 && g.batch == 1 && l <= 28)
-                return fix ? long_pole_split<T, OP, sizeof(T) == 8>(u, l, st) : long_pole_split<T, OP, false>(u, l, st);
+            if ((OP == OP_H || OP == OP_D) && g.d == 1 && g.batch == 1 && l <= 28)
+                return fix ? long_pole_split<T, OP, kFixable>(u, l, st) : long_pole_split<T, OP, false>(u, l, st);
             return sweep_level<T, OP>(u, g, 0, st);
         }
-        return fix ? launch_group<T, OP, sizeof(T) == 8, true>(u, g, 0, st) : launch_group<T, OP, false, true>(u, g, 0, st);
+        return fix ? launch_group<T, OP, kFixable, true>(u, g, 0, st) : launch_group<T, OP, false, true>(u, g, 0, st);
     }
-    if (fix && g.n[k] <= kGroupElems) return launch_group<T, OP, sizeof(T) == 8, false>(u, g, k, st);
+    if (fix && g.n[k] <= kGroupElems) return launch_group<T, OP, kFixable, false>(u, g, k, st);
     // fp32 poles of 65 points still fit in registers
     if constexpr (sizeof(T) == 4)
         if (l == kRegPoleMaxLevel + 1) return launch_pole_regs<T, OP, kRegPoleMaxLevel + 1>(u, g.S[k], poles, st);
@@ -526,6 +580,7 @@ int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed)
         case OP_H: return plain_all<T, OP_H>(u, g, st, fixed);
         case OP_D: return plain_all<T, OP_D>(u, g, st, fixed);
         case OP_A: return plain_all<T, OP_A>(u, g, st, fixed);
+        case OP_DT: return plain_all<T, OP_DT>(u, g, st, false);
         default: return GBH_EINVAL;
     }
 }

@@ -1916,7 +1916,7 @@ int gbh_plan_bind(gbh_plan *plan, void *const *grid_ptrs, void *stream)
 int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
 {
     if (!plan) return GBH_EINVAL;
-    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return op == GBH_ADJOINT ? GBH_EUNSUPPORTED : GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return (op == GBH_ADJOINT || op == GBH_DEHIERARCHIZE_ADJOINT) ? GBH_EUNSUPPORTED : GBH_EINVAL;
     if (!plan->bound) return GBH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // queue, status and counters restart with every execution
@@ -2117,7 +2117,7 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
 {
     if (!levels || !grid_ptrs || n_grids < 1 || d < 1 || d > kPlanMaxD) return GBH_EINVAL;
     if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
-    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return op == GBH_ADJOINT ? GBH_EUNSUPPORTED : GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return (op == GBH_ADJOINT || op == GBH_DEHIERARCHIZE_ADJOINT) ? GBH_EUNSUPPORTED : GBH_EINVAL;
     if (n_grids > kNoAllocMaxGrids) return GBH_ERANGE;
     const size_t es = dtype == GBH_F64 ? 8 : 4;
     // per-grid geometry

@@ -11,7 +11,7 @@ from paper_1309_0392_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 gbh = pytest.importorskip("paper_1309_0392_gb300")
-from paper_1309_0392_gb300.autograd import HierarchizeFn  # noqa: E402
+from paper_1309_0392_gb300.autograd import DehierarchizeFn, HierarchizeFn  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -112,3 +112,18 @@ def test_central_differences_full_workload():
         fd = (grid_loss(up) - grid_loss(dn)) / (2 * eps)
         gc = g[b, c].item()
         assert abs(fd - gc) <= 1e-6 * max(abs(gc), 1e-3 * gmax), (b, c, fd, gc)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+def test_dehierarchize_fn_gradient(dtype, tol):
+    """d/d alpha of <D alpha, w> is D^T w (the oracle's transpose)."""
+    levels = (5, 4, 3)
+    rng = np.random.default_rng(17)
+    a = rng.uniform(-1, 1, inputs.num_points(levels))
+    w = rng.uniform(-1, 1, a.size)
+    alpha = torch.tensor(a, dtype=dtype, device="cuda", requires_grad=True)
+    u = DehierarchizeFn.apply(alpha, levels)
+    (u * torch.tensor(w, dtype=dtype, device="cuda")).sum().backward()
+    ref = oracle.dehierarchize_adjoint(w, levels)
+    assert np.abs(alpha.grad.double().cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
+    assert np.abs(u.detach().double().cpu().numpy() - oracle.dehierarchize(a, levels)).max() <= tol * 8

@@ -17,8 +17,10 @@ gbh = pytest.importorskip("paper_1309_0392_gb300")
 
 pytestmark = pytest.mark.gpu
 
-OPS = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}
-ORACLE = {"h": oracle.hierarchize, "d": oracle.dehierarchize, "a": oracle.hierarchize_adjoint}
+OPS = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT,
+       "t": gbh.GBH_DEHIERARCHIZE_ADJOINT}
+ORACLE = {"h": oracle.hierarchize, "d": oracle.dehierarchize, "a": oracle.hierarchize_adjoint,
+          "t": oracle.dehierarchize_adjoint}
 TOL64 = 1e-13
 TOL32 = 1e-5
 
@@ -174,7 +176,26 @@ def test_long_pole_split(levels, op):
     assert rel_err(run(u, levels, op), ref, u) <= TOL64
 
 
-@pytest.mark.parametrize("op", ["h", "d", "a"])
+@pytest.mark.parametrize("levels", LEVELS + [(16,), (2, 13), (14, 1, 1, 1), (1, 1, 14), (6,) * 3])
+def test_dehierarchize_adjoint(levels):
+    """Transpose of the dehierarchization: native on every path, in the serial
+    operation order, so fp64 is bit-exact; fp32 within the tolerance."""
+    u = inputs.uniform(levels, 13)
+    ref = ORACLE["t"](u, levels)
+    assert np.array_equal(run(u, levels, "t", path=gbh.GBH_PATH_PLAIN), ref)
+    assert np.array_equal(run(u, levels, "t"), ref)
+    u32 = u.astype(np.float32).astype(np.float64)
+    assert rel_err(run(u32, levels, "t", dtype=torch.float32), ORACLE["t"](u32, levels), u32) <= TOL32
+
+
+def test_dehierarchize_adjoint_unsupported_paths():
+    t = torch.zeros(inputs.num_points((4, 4)), dtype=torch.float64, device="cuda")
+    for path in (gbh.GBH_PATH_FUSED, gbh.GBH_PATH_GROUPED):
+        with pytest.raises(gbh.GbhError):
+            gbh.transform(t, (4, 4), gbh.GBH_DEHIERARCHIZE_ADJOINT, path=path)
+
+
+@pytest.mark.parametrize("op", ["h", "d", "a", "t"])
 def test_same_shape_batch(op):
     levels, B = (4, 3, 5), 5
     n = inputs.num_points(levels)
