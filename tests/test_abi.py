@@ -58,6 +58,21 @@ def test_argument_errors_launch_nothing(L):
     opt.path = 7
     assert L.gbh_transform(fake, 2, lv, 1, 0, ctypes.byref(opt), None) == -1   # path
     assert L.gbh_transform_batched(fake, 0, 2, lv, 1, 0, None, None) == -1     # batch
+    # the transpose of the dehierarchization runs on the per-dimension path only
+    for path in (2, 3):                                                        # fused, grouped
+        opt.path = path
+        assert L.gbh_transform(fake, 2, lv, 1, 3, ctypes.byref(opt), None) == -8
+    # scheme plans: invalid arguments and owned-grid lists fail before any
+    # device allocation
+    h = ctypes.c_void_p()
+    assert L.gbh_plan_create_scheme(0, 4, 1, ctypes.byref(h)) == -1
+    assert L.gbh_plan_create_scheme(3, 4, 7, ctypes.byref(h)) == -2
+    for owned in ([], [3, 1], [0, 0], [-1], [10 ** 6]):
+        arr = _lib.levels_arg(owned) if owned else None
+        assert L.gbh_plan_create_scheme_subset(3, 4, 1, len(owned), arr, ctypes.byref(h)) == -1
+    assert not h.value
+    assert L.gbh_plan_scatter(None, fake, 0, None) == -1
+    assert L.gbh_plan_gather(None, fake, None) == -1
     assert _lib.launch_count() == before
 
 
