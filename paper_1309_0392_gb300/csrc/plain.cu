@@ -167,10 +167,14 @@ __global__ void __launch_bounds__(256) k_level(T *__restrict__ u, int64_t S, int
         T *p = u + o * S * n + j;
         if (OP == OP_A || OP == OP_DT) {
             const int64_t i = 2 * s * q;
-            const T h = OP == OP_A ? T(-0.5) : T(0.5);
             T y = p[i * S];
-            if (q > 0) y = y + h * p[(i - s) * S];
-            if (q < per - 1) y = y + h * p[(i + s) * S];
+            if (OP == OP_A) {
+                if (q > 0) y = y - T(0.5) * p[(i - s) * S];
+                if (q < per - 1) y = y - T(0.5) * p[(i + s) * S];
+            } else {
+                if (q > 0) y = y + T(0.5) * p[(i - s) * S];
+                if (q < per - 1) y = y + T(0.5) * p[(i + s) * S];
+            }
             p[i * S] = y;
         } else {
             const int64_t i = (2 * q + 1) * s;
