@@ -44,8 +44,9 @@ def _stream_ptr(t, stream):
 def transform(t, levels, op=GBH_HIERARCHIZE, *, path=GBH_PATH_AUTO, tile=None, arith=0,
               stream=None, batch=None):
     """In-place transform of grid tensor ``t`` (op: GBH_HIERARCHIZE,
-    GBH_DEHIERARCHIZE, GBH_ADJOINT or GBH_DEHIERARCHIZE_ADJOINT).  With ``batch=B`` the tensor holds B
-    grids of the level vector back to back.  Returns ``t``."""
+    GBH_DEHIERARCHIZE, GBH_ADJOINT or GBH_DEHIERARCHIZE_ADJOINT).  With
+    ``batch=B`` the tensor holds B grids of the level vector back to back.
+    Returns ``t``."""
     B = 1 if batch is None else int(batch)
     if B < 1:
         raise ValueError("batch must be >= 1")
