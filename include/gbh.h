@@ -57,7 +57,8 @@ typedef enum {
     GBH_HIERARCHIZE = 0,    /* nodal -> hierarchical (Alg. 1)                    */
     GBH_DEHIERARCHIZE = 1,  /* hierarchical -> nodal (inverse of Alg. 1)         */
     GBH_ADJOINT = 2,        /* transpose of Alg. 1                               */
-    GBH_DEHIERARCHIZE_ADJOINT = 3  /* transpose of the inverse (plain path only)  */
+    GBH_DEHIERARCHIZE_ADJOINT = 3  /* transpose of the inverse (per-dimension path,
+                                      native arithmetic whatever `arith` says)  */
 } gbh_op;
 
 /* ------------------------------------------------------------------------ */
@@ -110,7 +111,9 @@ typedef enum {
     GBH_PATH_AUTO = 0,   /* planner's choice (fused when available)             */
     GBH_PATH_PLAIN = 1,  /* one sweep kernel per dimension (native arithmetic
                             unless arith = 2)                                   */
-    GBH_PATH_FUSED = 2,  /* dyadic-tile kernels, all dimensions per tile        */
+    GBH_PATH_FUSED = 2,  /* dyadic-tile kernels, all dimensions per tile
+                            (hierarchize and dehierarchize, d in [2, 6];
+                            GBH_EUNSUPPORTED otherwise)                         */
     GBH_PATH_GROUPED = 3 /* one pass per group of consecutive dimensions whose
                             pole sets fit in a shared-memory tile (hierarchize
                             and dehierarchize; GBH_EUNSUPPORTED for a level of
@@ -131,7 +134,7 @@ typedef struct {
 } gbh_options;
 
 /*
- * General form of the three single-grid calls with an explicit op and
+ * General form of the four single-grid calls with an explicit op and
  * execution options (NULL = defaults).  Used by tests and the tuner to pin a
  * path; the results of every path agree with the oracle within the stated
  * tolerance.
