@@ -39,7 +39,7 @@ def rel_err(a, b, u):
 
 
 @pytest.mark.parametrize("op,name", [("h", "cfg1a_hierarchize.txt"), ("d", "cfg1a_dehierarchize.txt"),
-                                     ("a", "cfg1a_adjoint.txt")])
+                                     ("a", "cfg1a_adjoint.txt"), ("t", "cfg1a_dehier_adjoint.txt")])
 @pytest.mark.parametrize("path", [gbh.GBH_PATH_PLAIN, gbh.GBH_PATH_AUTO])
 def test_cfg1a_golden(op, name, path):
     levels, u = inputs.cfg1a()

@@ -11,6 +11,17 @@ def test_cfg1a_golden(orc):
     assert np.array_equal(orc.hierarchize(u, levels), load("cfg1a_hierarchize.txt"))
     assert np.array_equal(orc.dehierarchize(u, levels), load("cfg1a_dehierarchize.txt"))
     assert np.array_equal(orc.hierarchize_adjoint(u, levels), load("cfg1a_adjoint.txt"))
+    assert np.array_equal(orc.dehierarchize_adjoint(u, levels), load("cfg1a_dehier_adjoint.txt"))
+
+
+def test_scheme_gather_and_scatter_golden(orc):
+    d, n = 2, 4
+    lv, c = orc.scheme(d, n)
+    alphas = [orc.hierarchize(inputs.scheme_grid(l, 1000 + g), l) for g, l in enumerate(lv)]
+    sparse = orc.gather(d, n, lv, c, alphas)
+    assert np.array_equal(sparse, load("scheme_2_4_gather.txt"))
+    back = np.concatenate(orc.scatter(d, n, lv, c, sparse))
+    assert np.array_equal(back, load("scheme_2_4_scatter.txt"))
 
 
 def test_cfg1b_golden_is_closed_form(orc):
