@@ -195,6 +195,36 @@ def test_dehierarchize_adjoint_unsupported_paths():
             gbh.transform(t, (4, 4), gbh.GBH_DEHIERARCHIZE_ADJOINT, path=path)
 
 
+def test_headline_workload_full_size():
+    """The headline workload at full size in the bench's launch configuration:
+    level (9,9,9) (135 M points, fp64), the bench's input recipe, the default
+    path.  Hierarchization against the oracle at every point, then the
+    dehierarchization of that result against the oracle's, and the round trip."""
+    levels, u = inputs.cfg2()
+    t = torch.tensor(u, device="cuda")
+    gbh.hierarchize(t, levels)
+    torch.cuda.synchronize()
+    alpha = t.cpu().numpy()
+    assert rel_err(alpha, oracle.hierarchize(u, levels), u) <= TOL64
+    gbh.dehierarchize(t, levels)
+    torch.cuda.synchronize()
+    back = t.cpu().numpy()
+    assert rel_err(back, oracle.dehierarchize(alpha, levels), u) <= TOL64
+    assert rel_err(back, u, u) <= TOL64
+
+
+def test_fp32_form_full_size():
+    """The fp32 workload at full size: level (6,6,5,5,5), 152 M points, the
+    bench's input recipe, default path, against the oracle on the fp32 input."""
+    levels, u = inputs.cfg3()
+    u32 = u.astype(np.float32)
+    ref_in = u32.astype(np.float64)
+    t = torch.tensor(u32, device="cuda")
+    gbh.hierarchize(t, levels)
+    torch.cuda.synchronize()
+    assert rel_err(t.cpu().double().numpy(), oracle.hierarchize(ref_in, levels), ref_in) <= TOL32
+
+
 @pytest.mark.parametrize("op", ["h", "d", "a", "t"])
 def test_same_shape_batch(op):
     levels, B = (4, 3, 5), 5
