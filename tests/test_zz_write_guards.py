@@ -1,7 +1,9 @@
 """Guard words around device buffers: every path and operation writes only
 inside its grid (and a plan only inside its grids and its sparse vector).
 The grid is a view into a larger buffer whose first and last GUARD elements
-hold a sentinel; after the call they must be unchanged."""
+hold a sentinel; after the call they must be unchanged.
+
+Kept in a file that pytest collects last, after the parity tests."""
 import numpy as np
 import pytest
 
