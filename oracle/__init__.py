@@ -195,6 +195,22 @@ def gather(d: int, n: int, levels, coeffs, grids):
     return out
 
 
+def gather_exact(d: int, n: int, levels, coeffs, grids):
+    """sparse = sum_g coeffs[g] * alpha_g summed exactly (rational arithmetic)
+    and rounded once to the nearest double: the reading of the gather (Sec. 2)
+    that does not depend on the order of the grids.  Pure Python, small
+    schemes only."""
+    from fractions import Fraction
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32).reshape(-1, d))
+    acc = [Fraction(0)] * sparse_num_points(d, n)
+    for l, c, g in zip(lv, np.asarray(coeffs, dtype=np.float64), grids):
+        idx = sparse_index_of_grid(d, n, l)
+        cf = Fraction(float(c))
+        for f, v in enumerate(np.asarray(g, dtype=np.float64).reshape(-1)):
+            acc[idx[f]] += cf * Fraction(float(v))
+    return np.array([float(a) for a in acc], dtype=np.float64)
+
+
 def scatter(d: int, n: int, levels, coeffs, sparse, scaled: bool = False):
     """alpha_g = sparse restricted to the points of grid g (times coeffs[g]
     when scaled: the transpose of gather); one array per grid."""

@@ -482,6 +482,25 @@ def test_iterated_round_gives_sparse_interpolant(orc, d, n):
             assert g[f] == pytest.approx(want, abs=1e-13)
 
 
+@pytest.mark.parametrize("d,n", [(2, 3), (3, 3)])
+def test_exact_gather_is_order_free_and_close_to_the_ordered_one(orc, d, n):
+    """The exactly rounded gather: equal to the ordered fma gather when every
+    partial sum is exact (few mantissa bits), independent of the grid order,
+    and within a few units of the last place of the ordered gather on
+    general data."""
+    lv, c = orc.scheme(d, n)
+    rng = np.random.default_rng(23)
+    dyadic = [rng.integers(-64, 65, orc.num_points(l)) / 64.0 for l in lv]
+    assert np.array_equal(orc.gather_exact(d, n, lv, c, dyadic), orc.gather(d, n, lv, c, dyadic))
+    grids = [rng.uniform(-1, 1, orc.num_points(l)) for l in lv]
+    exact = orc.gather_exact(d, n, lv, c, grids)
+    perm = rng.permutation(len(lv))
+    assert np.array_equal(orc.gather_exact(d, n, lv[perm], c[perm], [grids[i] for i in perm]), exact)
+    ordered = orc.gather(d, n, lv, c, grids)
+    bound = len(lv) * np.finfo(float).eps * sum(abs(cg) * np.abs(g).max() for cg, g in zip(c, grids))
+    assert np.abs(ordered - exact).max() <= bound
+
+
 def test_level_weights(orc):
     levels = (2, 1)
     w = orc.level_weights(levels).reshape(3, 5)
