@@ -541,7 +541,8 @@ def run_case(args):
             "grouped": gbh.GBH_PATH_GROUPED}[extra[0] if extra else "auto"]
     arith = int(extra[1]) if len(extra) > 1 else 0
     dtype = torch.float64 if dt == "f64" else torch.float32
-    opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT}[op]
+    opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT,
+           "t": gbh.GBH_DEHIERARCHIZE_ADJOINT}[op]
     gen = torch.Generator(device="cuda").manual_seed(1)
     if kind == "transform":
         levels = tuple(int(v) for v in spec.split(","))
@@ -586,7 +587,7 @@ def main():
     ap.add_argument("--forms", action="store_true", default=True)
     ap.add_argument("--no-forms", dest="forms", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--case", default=None, help="profiling mode, e.g. transform:9,9,8:h:f64")
+    ap.add_argument("--case", default=None, help="profiling mode, e.g. transform:9,9,8:h:f64 (op h, d, a or t), batched:4,14:h:f64, gather:4,14:h:f64, scatter:4,14:h:f64")
     args = ap.parse_args()
     if args.case:
         run_case(args)
