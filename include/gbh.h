@@ -295,10 +295,32 @@ int gbh_sparse_index_of_grid(int d, int n, const int32_t *levels, int64_t *out);
  * up the array's device address; make that call before any stream capture.
  * Every call rewrites the shared array and clears its counters: calls whose
  * kernels overlap on the GPU (other streams, other threads) race, so order
- * them on one stream.  Not thread-safe on the host.
+ * them on one stream.  Not thread-safe on the host.  The return code covers
+ * argument and launch errors only; a bounded device-side wait that gives up
+ * (the grids' contents are then unspecified) is reported by
+ * gbh_batched_transform_noalloc_status.
  */
 int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, void *const *grid_ptrs,
                                   int dtype, int op, void *stream);
+
+/*
+ * Device-side status of the allocation-free transform on the current device:
+ * GBH_ETIMEOUT if a bounded wait of any call since the last read gave up,
+ * else GBH_OK (GBH_ECUDA if the status could not be read).  The word lives in
+ * the same fixed array, outside the part that every call clears, so it stays
+ * set across later calls until this function reads it; reading it clears it.
+ * Synchronises `stream` (cudaStream_t as void*).  Allocates nothing.
+ */
+int gbh_batched_transform_noalloc_status(void *stream);
+
+/*
+ * Failure injection for tests of the allocation-free transform: with
+ * grid >= 0, the following calls make every work item of grid `grid` wait for
+ * a dependency that is never released; the waits give up after `spin_limit`
+ * polls and set the status word.  grid = -1 restores normal operation.  Host
+ * state only; no GPU fault, trap or hang is involved.
+ */
+int gbh_batched_transform_noalloc_test_stall(int grid, long long spin_limit);
 
 /*
  * Failure injection for tests.  With grid >= 0, the next executions of the plan
@@ -310,13 +332,22 @@ int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *levels, voi
  */
 int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit);
 
-/* Sticky device-side status of a plan (GBH_ETIMEOUT after an expired wait);
- * synchronises the stream given.  Reading it clears it. */
+/* Sticky device-side status of a plan: GBH_ETIMEOUT if a bounded wait of any
+ * execution since the last read gave up, else GBH_OK.  Later executions do
+ * not clear it; reading it does.  Synchronises the stream given. */
 int gbh_plan_status(gbh_plan *plan, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                                */
 /* ------------------------------------------------------------------------ */
+
+/*
+ * Device-side status of the single-grid kernels: GBH_ETIMEOUT if a bounded
+ * wait of one of their kernels gave up since the last read (the data of that
+ * call is then unspecified), else GBH_OK.  One word per device in the library
+ * (no allocation); reading it clears it.  Synchronises `stream` first.
+ */
+int gbh_device_status(void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *gbh_status_string(int status);

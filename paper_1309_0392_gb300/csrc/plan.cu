@@ -149,7 +149,8 @@ struct BatchParams {
     const int *need;     // items per (grid, phase)
     int *emax;           // per grid
     unsigned *ticket;
-    int *status;
+    int *status;         // this launch: nonzero stops every CTA
+    int *sticky;         // kept across launches until read by a status call
     int op;
     long long spin_limit;   // bounded waits: polls before giving up
     int stall_grid;         // test hook: every item of this grid waits on a
@@ -351,7 +352,12 @@ __device__ __forceinline__ int next_item(const BatchParams &P, int *s_item, int 
                 const int *cnt = P.done + it.grid * kPhases + wait;
                 long long spins = 0;
                 while (ld_acquire(cnt) < want) {
-                    if (++spins > P.spin_limit) { atomicExch(P.status, GBH_ETIMEOUT); *s_abort = 1; break; }
+                    if (++spins > P.spin_limit) {
+                        atomicExch(P.status, GBH_ETIMEOUT);
+                        atomicExch(P.sticky, GBH_ETIMEOUT);
+                        *s_abort = 1;
+                        break;
+                    }
                     __nanosleep(64);
                 }
             }
@@ -1502,7 +1508,7 @@ struct gbh_plan {
     int *d_need[2] = {nullptr, nullptr};
     void **d_ptrs = nullptr;
     double *d_coeffs = nullptr;
-    unsigned char *d_scratch = nullptr;   // ticket | status | emax[G] | done[G][kPhases]
+    unsigned char *d_scratch = nullptr;   // ticket | status | emax[G] | done[G][kPhases] | sticky status
     size_t scratch_bytes = 0;
     int64_t *d_sub_off = nullptr;
     int *d_sub_j = nullptr, *d_list_off = nullptr, *d_list = nullptr;
@@ -1667,9 +1673,11 @@ int finish_plan(gbh_plan *p)
     if (int e = upload(&p->d_info, p->info)) return e;
     if (int e = upload(&p->d_coeffs, p->coeffs)) return e;
     if (cudaMalloc(reinterpret_cast<void **>(&p->d_ptrs), sizeof(void *) * p->ngrids) != cudaSuccess) return GBH_ENOMEM;
-    p->scratch_bytes = 64 + sizeof(int) * (size_t)p->ngrids * (1 + kPhases);
-    if (cudaMalloc(reinterpret_cast<void **>(&p->d_scratch), p->scratch_bytes) != cudaSuccess) return GBH_ENOMEM;
-    if (cudaMemset(p->d_scratch, 0, p->scratch_bytes) != cudaSuccess) return GBH_ECUDA;
+    // the per-execution part (cleared by every execution), then the sticky
+    // status word behind it
+    p->scratch_bytes = (64 + sizeof(int) * (size_t)p->ngrids * (1 + kPhases) + 15) / 16 * 16;
+    if (cudaMalloc(reinterpret_cast<void **>(&p->d_scratch), p->scratch_bytes + 16) != cudaSuccess) return GBH_ENOMEM;
+    if (cudaMemset(p->d_scratch, 0, p->scratch_bytes + 16) != cudaSuccess) return GBH_ECUDA;
     if (cudaMallocHost(reinterpret_cast<void **>(&p->h_ptrs), sizeof(void *) * p->ngrids) != cudaSuccess) return GBH_ENOMEM;
     cudaGetDevice(&p->dev);
     return GBH_OK;
@@ -1928,6 +1936,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
     P.ptrs = plan->d_ptrs;
     P.ticket = reinterpret_cast<unsigned *>(plan->d_scratch);
     P.status = reinterpret_cast<int *>(plan->d_scratch + 32);
+    P.sticky = reinterpret_cast<int *>(plan->d_scratch + plan->scratch_bytes);
     P.emax = reinterpret_cast<int *>(plan->d_scratch + 64);
     P.done = P.emax + plan->ngrids;
     P.need = plan->d_need[op];
@@ -2063,12 +2072,13 @@ int gbh_plan_status(gbh_plan *plan, void *stream)
     if (!plan) return GBH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int st = 0;
-    if (cudaMemcpyAsync(&st, plan->d_scratch + 32, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    unsigned char *word = plan->d_scratch + plan->scratch_bytes;
+    if (cudaMemcpyAsync(&st, word, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return GBH_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
     if (st != 0) {
-        const int zero = 0;
-        cudaMemcpy(plan->d_scratch + 32, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (cudaMemsetAsync(word, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return GBH_ECUDA;
     }
     return st;
 }
@@ -2088,7 +2098,9 @@ int gbh_plan_status(gbh_plan *plan, void *stream)
 // is looked up once per device (the first call on a device does this, so that
 // call should come before any stream capture).  Every call shares the array
 // and rewrites it: calls that overlap on the GPU race; the counters are
-// cleared by every call.
+// cleared by every call.  The first 256 bytes hold a status word that no call
+// clears: a bounded wait that gives up sets it to GBH_ETIMEOUT, and
+// gbh_batched_transform_noalloc_status reads and clears it.
 
 namespace {
 
@@ -2107,8 +2119,24 @@ struct NoAllocHost {
 };
 static NoAllocHost g_na_host;                      // host staging, no heap
 static unsigned char *g_na_dev[64];                // symbol address per device
+static int g_na_stall_grid = -1;                   // failure injection (tests)
+static long long g_na_spin_limit = kSpinLimit;
 
 size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+
+// The array's device address on the current device (looked up once).
+unsigned char *na_base()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!g_na_dev[dev]) {
+        unsigned char *ptr = nullptr;
+        if (cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch) != cudaSuccess || !ptr)
+            return nullptr;
+        g_na_dev[dev] = ptr;
+    }
+    return g_na_dev[dev];
+}
 
 }  // namespace
 
@@ -2151,8 +2179,8 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
         g_na_host.ptrs[g] = grid_ptrs[g];
         g_na_host.order[g] = g;
     }
-    // device layout: counters | need | ptrs | info | items
-    const size_t o_ticket = 0, o_status = 32, o_emax = 64;
+    // device layout: sticky status | counters | need | ptrs | info | items
+    const size_t o_sticky = 0, o_ticket = 256, o_status = 288, o_emax = 320;
     const size_t o_done = na_align(o_emax + sizeof(int) * (size_t)n_grids);
     const size_t o_need = na_align(o_done + sizeof(int) * (size_t)n_grids * kPhases);
     const size_t o_ptrs = na_align(o_need + sizeof(int) * (size_t)n_grids * kPhases);
@@ -2172,32 +2200,27 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
                                 });
     if (!ok) return GBH_ERANGE;
     // set-up: the array's device address, once per device
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GBH_ECUDA;
-    if (!g_na_dev[dev]) {
-        unsigned char *ptr = nullptr;
-        if (cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch) != cudaSuccess || !ptr)
-            return GBH_ECUDA;
-        g_na_dev[dev] = ptr;
-    }
-    unsigned char *base = g_na_dev[dev];
+    unsigned char *base = na_base();
+    if (!base) return GBH_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // counters start at zero; the tables are rewritten by every call
-    if (cudaMemsetAsync(base, 0, o_need, s) != cudaSuccess) return GBH_ECUDA;
+    // counters start at zero; the tables are rewritten by every call; the
+    // sticky status word is left alone
+    if (cudaMemsetAsync(base + o_ticket, 0, o_need - o_ticket, s) != cudaSuccess) return GBH_ECUDA;
     if (cudaMemcpyAsync(base + o_need, g_na_host.need, sizeof(int) * (size_t)n_grids * kPhases, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(base + o_ptrs, g_na_host.ptrs, sizeof(void *) * (size_t)n_grids, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(base + o_info, g_na_host.info, sizeof(GridInfo) * (size_t)n_grids, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(base + o_items, g_na_host.items, sizeof(Item) * (size_t)nitems, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return GBH_ECUDA;
     BatchParams P{};
-    P.spin_limit = kSpinLimit;
-    P.stall_grid = -1;
+    P.spin_limit = g_na_spin_limit;
+    P.stall_grid = g_na_stall_grid < n_grids ? g_na_stall_grid : -1;
     P.items = reinterpret_cast<const Item *>(base + o_items);
     P.nitems = nitems;
     P.grids = reinterpret_cast<const GridInfo *>(base + o_info);
     P.ptrs = reinterpret_cast<void *const *>(base + o_ptrs);
     P.ticket = reinterpret_cast<unsigned *>(base + o_ticket);
     P.status = reinterpret_cast<int *>(base + o_status);
+    P.sticky = reinterpret_cast<int *>(base + o_sticky);
     P.emax = reinterpret_cast<int *>(base + o_emax);
     P.done = reinterpret_cast<int *>(base + o_done);
     P.need = reinterpret_cast<const int *>(base + o_need);
@@ -2217,4 +2240,28 @@ extern "C" int gbh_batched_transform_noalloc(int n_grids, int d, const int32_t *
     if (dtype == GBH_F64)
         return op == GBH_HIERARCHIZE ? launch(k_batched<double, OP_H>) : launch(k_batched<double, OP_D>);
     return op == GBH_HIERARCHIZE ? launch(k_batched<float, OP_H>) : launch(k_batched<float, OP_D>);
+}
+
+extern "C" int gbh_batched_transform_noalloc_status(void *stream)
+{
+    unsigned char *base = na_base();
+    if (!base) return GBH_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st = 0;    // pageable host memory: the copy has completed when the call returns
+    if (cudaMemcpyAsync(&st, base, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GBH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GBH_ECUDA;
+    const int out = st;
+    if (out != 0) {
+        if (cudaMemsetAsync(base, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+            return GBH_ECUDA;
+    }
+    return out;
+}
+
+extern "C" int gbh_batched_transform_noalloc_test_stall(int grid, long long spin_limit)
+{
+    if (grid < -1 || grid >= kNoAllocMaxGrids || spin_limit < 1) return GBH_EINVAL;
+    g_na_stall_grid = grid;
+    g_na_spin_limit = grid < 0 ? kSpinLimit : spin_limit;
+    return GBH_OK;
 }
