@@ -341,14 +341,6 @@ int gbh_plan_status(gbh_plan *plan, void *stream);
 /* Diagnostics                                                                */
 /* ------------------------------------------------------------------------ */
 
-/*
- * Device-side status of the single-grid kernels: GBH_ETIMEOUT if a bounded
- * wait of one of their kernels gave up since the last read (the data of that
- * call is then unspecified), else GBH_OK.  One word per device in the library
- * (no allocation); reading it clears it.  Synchronises `stream` first.
- */
-int gbh_device_status(void *stream);
-
 /* Human-readable name of a status code (static string). */
 const char *gbh_status_string(int status);
 

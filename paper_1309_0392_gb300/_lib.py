@@ -74,7 +74,6 @@ _SIGS = {
                                                      ctypes.c_int, ctypes.c_int, _VP]),
     "gbh_batched_transform_noalloc_status": (ctypes.c_int, [_VP]),
     "gbh_batched_transform_noalloc_test_stall": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
-    "gbh_device_status": (ctypes.c_int, [_VP]),
     "gbh_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gbh_launch_count": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "gbh_version": (ctypes.c_int, []),

@@ -1426,14 +1426,6 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
         // classes with a compile-time kernel go one by one, the rest together
         std::vector<ClassPlan> rest;
         for (const ClassPlan &cp : pl.by_size[c]) {
-            if constexpr (FIX && sizeof(ST) == 8) {
-                // the interior class of a 3-D grid: persistent pipelined kernel
-                if (cp.mask == 0 && cp.npoint == 0) {
-                    const int r = interior3_transform(reinterpret_cast<double *>(u), g, pl.m, OP, st);
-                    if (r == GBH_OK) continue;
-                    if (r != 1) return r;
-                }
-            }
             const int r = launch_tile3<ST, FIX, OP>(pl, cp, g, u, st);
             if (r == 1) rest.push_back(cp);
             else if (r != GBH_OK) return r;

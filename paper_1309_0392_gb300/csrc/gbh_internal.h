@@ -71,9 +71,4 @@ bool fused_preferred(const Geom &g, int dtype, int op);
 // True if the fused path supports this (geometry, dtype, op).
 bool fused_supported(const Geom &g, int dtype, int op);
 
-// Interior class of a 3-D fp64 grid with tile exponents m (fixed point):
-// persistent pipelined kernel.  Returns 1 if no compiled tile matches (the
-// caller then uses the per-closure kernel), else a status.
-int interior3_transform(double *u, const Geom &g, const int *m, int op, cudaStream_t s);
-
 }  // namespace gbh

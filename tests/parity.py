@@ -3,10 +3,13 @@
 The tolerances are relative to max|u|, u the nodal vector of the transform
 (the reading of "relative to max|u|" for every operation):
 
-- hierarchization, its transpose and the transpose of the inverse: u is the
-  input;
+- hierarchization and its transpose: u is the input;
 - dehierarchization: u is its output, the nodal side (the reference output
-  of the oracle).
+  of the oracle);
+- transpose of the dehierarchization: its output, the side that accumulates
+  (every point collects half of each descendant's value, so a coarse point's
+  output is a sum of up to 2^l terms, as every nodal value of the
+  dehierarchization is a sum over its predecessors).
 
 Bounds for composite steps (the gather of a combination scheme, a round of
 the iterated combination technique) are derived from these per-point
@@ -23,9 +26,9 @@ EPS64 = 2.0 ** -53
 
 
 def nodal_scale(u_in, ref, op):
-    """max|u| of the nodal vector of op ('h', 'a', 't': the input; 'd': the
+    """max|u| of the nodal vector of op ('h', 'a': the input; 'd', 't': the
     reference output)."""
-    side = ref if op == "d" else u_in
+    side = ref if op in ("d", "t") else u_in
     return max(float(np.abs(np.asarray(side, dtype=np.float64)).max()) if np.size(side) else 0.0, 1e-300)
 
 
