@@ -164,6 +164,48 @@ int gbh_num_points(int d, const int32_t *levels, int64_t *out);
 int gbh_tile_plan(int d, const int32_t *levels, int dtype, int op, int32_t *m_out);
 
 /* ------------------------------------------------------------------------ */
+/* Autotuner                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The tile shapes gbh_autotune times on the fused path for (d, levels, dtype,
+ * op), best estimate first: up to max_count vectors of d tile exponents into
+ * m_out (host array [max_count][d]), their number into *count.  Host only.
+ * GBH_EUNSUPPORTED if the fused path does not take the shape.
+ */
+int gbh_tile_candidates(int d, const int32_t *levels, int dtype, int op, int max_count, int32_t *m_out, int *count);
+
+/* Outcome of gbh_autotune. */
+typedef struct {
+    int32_t path;              /* chosen gbh_path: GBH_PATH_PLAIN, _FUSED or _GROUPED */
+    int32_t tile_exp[16];      /* GBH_PATH_FUSED: chosen tile exponents m_k          */
+    int32_t candidates;        /* configurations timed                               */
+    double ms_tuned;           /* median time of the chosen configuration            */
+    double ms_model;           /* median time of the cost model's configuration      */
+    int32_t model_path;        /* the cost model's configuration                     */
+    int32_t model_tile_exp[16];
+    int32_t reserved[4];
+} gbh_tune_result;
+
+/*
+ * Measured choice of the execution path and of the dyadic tile shape for one
+ * level vector (the dimension fusion and tile shape per level vector; the
+ * cost model alone ranks tiles by estimated DRAM bytes).  Times, on a scratch
+ * grid of that shape allocated for the call (values in [-1, 1)), the
+ * per-dimension sweeps, the six best-estimated tile shapes of the dyadic path
+ * and the dimension-group path (each the median of three runs), and records
+ * the fastest: later gbh_transform calls with the default path
+ * (GBH_PATH_AUTO, all tile_exp 0) and the four single-grid calls use it for
+ * this (d, levels, dtype, op).  The record lives in the process and is
+ * shared by all threads.  Synchronous; allocates and frees the scratch grid
+ * (twice the grid's bytes) on the current device.  GBH_ENOMEM if that fails.
+ */
+int gbh_autotune(int d, const int32_t *levels, int dtype, int op, gbh_tune_result *out);
+
+/* Drops every recorded choice: the cost model decides again. */
+int gbh_autotune_reset(void);
+
+/* ------------------------------------------------------------------------ */
 /* Combination scheme (Sec. 2): batched transform and sparse-grid gather     */
 /* ------------------------------------------------------------------------ */
 
@@ -321,6 +363,42 @@ int gbh_batched_transform_noalloc_status(void *stream);
  * state only; no GPU fault, trap or hang is involved.
  */
 int gbh_batched_transform_noalloc_test_stall(int grid, long long spin_limit);
+
+/*
+ * Execution parameters of gbh_plan_execute for op (GBH_HIERARCHIZE or
+ * GBH_DEHIERARCHIZE): resident CTAs per SM of the persistent kernel
+ * (0..32; 0 = as many as fit, more than fit = as many as fit) and the size in
+ * MiB of the L2 waves the work queue is ordered in (1..4096; grids are cut
+ * into waves of about that many bytes, items run along (wave, phase)
+ * diagonals).  Results do not depend on them.  Host call; when the wave
+ * changes it waits for the device to be idle, then rewrites the plan's work
+ * list.
+ */
+int gbh_plan_set_params(gbh_plan *plan, int op, int ctas_per_sm, int wave_mb);
+int gbh_plan_get_params(const gbh_plan *plan, int op, int *ctas_per_sm, int *wave_mb);
+
+/* Outcome of gbh_plan_autotune. */
+typedef struct {
+    int32_t ctas_per_sm;       /* chosen resident CTAs per SM                         */
+    int32_t wave_mb;           /* chosen L2 wave (MiB)                                */
+    int32_t candidates;        /* configurations timed                                */
+    int32_t max_ctas_per_sm;   /* the most that fit (the untuned setting)             */
+    double ms_tuned;           /* median time of the chosen configuration             */
+    double ms_model;           /* median time of the untuned configuration            */
+    int32_t reserved[4];
+} gbh_plan_tune_result;
+
+/*
+ * Measured choice of the execution parameters of op for this plan: times every
+ * CTAs-per-SM count that fits and L2 waves of 8, 16, 32 and 64 MiB (median of
+ * three executions each) on scratch grids of the plan's shapes (allocated for
+ * the call: the plan's total points of dtype; values in [-1, 1)), keeps the
+ * fastest in the plan and, for plans made by gbh_plan_create_scheme, for
+ * every later plan of the same (d, n, dtype) in this process.  The caller's
+ * bound grids are untouched and bound again afterwards.  Synchronises
+ * `stream`; GBH_ENOMEM if the scratch grids cannot be allocated.
+ */
+int gbh_plan_autotune(gbh_plan *plan, int op, void *stream, gbh_plan_tune_result *out);
 
 /*
  * Failure injection for tests.  With grid >= 0, the next executions of the plan

@@ -16,7 +16,7 @@ from ._lib import (GBH_ADJOINT, GBH_DEHIERARCHIZE, GBH_DEHIERARCHIZE_ADJOINT, GB
                    GBH_ARITH_NATIVE, GBH_ARITH_FIXED, GbhError, sparse_index_of_grid)
 
 __all__ = ["hierarchize", "dehierarchize", "hierarchize_adjoint", "dehierarchize_adjoint", "transform", "num_points",
-           "Plan", "HierarchizeFn", "DehierarchizeFn", "GbhError", "sparse_index_of_grid"]
+           "autotune", "autotune_reset", "Plan", "HierarchizeFn", "DehierarchizeFn", "GbhError", "sparse_index_of_grid"]
 
 
 def num_points(levels) -> int:
@@ -102,6 +102,25 @@ def hierarchize_adjoint(t, levels, **kw):
 def dehierarchize_adjoint(t, levels, **kw):
     """Transpose of :func:`dehierarchize` in place."""
     return transform(t, levels, GBH_DEHIERARCHIZE_ADJOINT, **kw)
+
+
+def autotune(levels, dtype="float64", op=GBH_HIERARCHIZE):
+    """Times the execution paths and tile shapes of the single-grid transform
+    for this level vector on a scratch grid and records the fastest for the
+    default path (gbh_autotune).  Returns the choice and the times."""
+    code = _lib.GBH_F64 if str(dtype).endswith("float64") else _lib.GBH_F32
+    r = _lib.TuneResult()
+    _lib.check(_lib.lib().gbh_autotune(len(levels), _lib.levels_arg(levels), code, int(op), ctypes.byref(r)),
+               "gbh_autotune")
+    d = len(levels)
+    return {"path": int(r.path), "tile_exp": tuple(int(v) for v in r.tile_exp[:d]), "candidates": int(r.candidates),
+            "ms_tuned": float(r.ms_tuned), "ms_model": float(r.ms_model), "model_path": int(r.model_path),
+            "model_tile_exp": tuple(int(v) for v in r.model_tile_exp[:d])}
+
+
+def autotune_reset():
+    """Drops every recorded autotuner choice (gbh_autotune_reset)."""
+    _lib.check(_lib.lib().gbh_autotune_reset(), "gbh_autotune_reset")
 
 
 from .plan import Plan  # noqa: E402

@@ -30,6 +30,18 @@ class GbhError(RuntimeError):
         super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("tile_exp", ctypes.c_int32 * 16), ("candidates", ctypes.c_int32),
+                ("ms_tuned", ctypes.c_double), ("ms_model", ctypes.c_double), ("model_path", ctypes.c_int32),
+                ("model_tile_exp", ctypes.c_int32 * 16), ("reserved", ctypes.c_int32 * 4)]
+
+
+class PlanTuneResult(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("wave_mb", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("max_ctas_per_sm", ctypes.c_int32), ("ms_tuned", ctypes.c_double), ("ms_model", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_exp", ctypes.c_int32 * 16),
                 ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
@@ -69,6 +81,14 @@ _SIGS = {
     "gbh_sparse_index_of_grid": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P,
                                                 ctypes.POINTER(ctypes.c_int64)]),
     "gbh_plan_status": (ctypes.c_int, [_VP, _VP]),
+    "gbh_plan_set_params": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "gbh_plan_get_params": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "gbh_plan_autotune": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.POINTER(PlanTuneResult)]),
+    "gbh_autotune": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(TuneResult)]),
+    "gbh_autotune_reset": (ctypes.c_int, []),
+    "gbh_tile_candidates": (ctypes.c_int, [ctypes.c_int, _I32P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I32P,
+                                           ctypes.POINTER(ctypes.c_int)]),
     "gbh_plan_test_stall": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_longlong]),
     "gbh_batched_transform_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _I32P, ctypes.POINTER(_VP),
                                                      ctypes.c_int, ctypes.c_int, _VP]),
@@ -178,3 +198,16 @@ def tile_plan(levels, dtype_code=GBH_F64, op=GBH_HIERARCHIZE):
         return None
     check(st, "gbh_tile_plan")
     return tuple(int(v) for v in out)
+
+
+def tile_candidates(levels, dtype_code=GBH_F64, op=GBH_HIERARCHIZE, max_count=6):
+    """Tile shapes the autotuner times on the fused path, best estimate first
+    ([] if the fused path does not take the shape).  Host only."""
+    d = len(levels)
+    out = (ctypes.c_int32 * (max_count * d))()
+    cnt = ctypes.c_int(0)
+    st = lib().gbh_tile_candidates(d, levels_arg(levels), dtype_code, op, max_count, out, ctypes.byref(cnt))
+    if st == -8:
+        return []
+    check(st, "gbh_tile_candidates")
+    return [tuple(int(out[i * d + k]) for k in range(d)) for i in range(cnt.value)]

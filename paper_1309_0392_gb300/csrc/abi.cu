@@ -142,6 +142,21 @@ int gbh_tile_plan(int d, const int32_t *levels, int dtype, int op, int32_t *m_ou
     return GBH_OK;
 }
 
+int gbh_tile_candidates(int d, const int32_t *levels, int dtype, int op, int max_count, int32_t *m_out, int *count)
+{
+    if (!m_out || !count || max_count < 1) return GBH_EINVAL;
+    if (dtype != GBH_F32 && dtype != GBH_F64) return GBH_EDTYPE;
+    Geom g;
+    if (int e = make_geom(d, levels, dtype == GBH_F64 ? 8 : 4, &g)) return e;
+    std::vector<std::vector<int>> c;
+    *count = 0;
+    if (!fused_candidates(g, dtype, op, max_count, &c)) return GBH_EUNSUPPORTED;
+    for (size_t i = 0; i < c.size(); ++i)
+        for (int k = 0; k < d; ++k) m_out[i * d + k] = c[i][k];
+    *count = (int)c.size();
+    return GBH_OK;
+}
+
 int gbh_transform(void *data, int d, const int32_t *levels, int dtype, int op,
                   const gbh_options *opt, void *stream)
 {
@@ -173,9 +188,14 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
         return fused_transform(data, g, dtype, op, opt, s);
     }
     if (path == GBH_PATH_GROUPED) return grouped_transform(data, g, dtype, op, s);
-    // planner's choice: the fused path when it takes the shape and the grid is
-    // large enough to tile, else one sweep per dimension
-    if (g.N >= 4096 && fused_preferred(g, dtype, op)) return fused_transform(data, g, dtype, op, opt, s);
+    // a choice the autotuner measured for this shape, else the cost model's:
+    // the fused path when it takes the shape and the grid is large enough to
+    // tile, else one sweep per dimension
+    const int tp = tuned_path(g, dtype, op);
+    if (tp == GBH_PATH_FUSED) return fused_transform(data, g, dtype, op, opt, s);
+    if (tp == GBH_PATH_GROUPED) return grouped_transform(data, g, dtype, op, s);
+    if (tp != GBH_PATH_PLAIN && g.N >= 4096 && fused_preferred(g, dtype, op))
+        return fused_transform(data, g, dtype, op, opt, s);
     // fp64 sweeps compute in fixed point unless native arithmetic is asked for
     return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1));
 }

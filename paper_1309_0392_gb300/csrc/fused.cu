@@ -1146,8 +1146,20 @@ double estimate_bytes(const Geom &g, const int *m, int es, int op, size_t cap, b
     return bytes;
 }
 
+// Plan cache: one class plan per (d, element size, op, levels), the cost
+// model's choice unless the autotuner pinned another one.
 std::mutex g_plan_mu;
 std::map<std::vector<int>, Plan> g_plans;
+
+std::vector<int> plan_key(const Geom &g, int es, int op)
+{
+    std::vector<int> key;
+    key.push_back(g.d);
+    key.push_back(es);
+    key.push_back(op);
+    for (int k = 0; k < g.d; ++k) key.push_back(g.l[k]);
+    return key;
+}
 
 bool tile3_shape_ok(int es, int E0, int E1, int E2);
 
@@ -1157,7 +1169,14 @@ bool tile3_shape_ok(int es, int E0, int E1, int E2);
 // the interior-class closure fits half the shared-memory budget (two CTAs
 // per SM).  Returns false when no such m exists (e.g. one very long
 // dimension): the plain path then takes the grid.
-bool choose_m(const Geom &g, int es, int op, int *m_out)
+// Feasible tile exponents ranked by estimated DRAM bytes (at most K):
+// every dimension of level >= 1 has a block interior (m_k >= 1); every
+// lattice extent 2^{l_k - m_k} + 1 and block extent 2^{m_k} + 1 fits a
+// register pole; the interior-class closure fits half the shared-memory
+// budget (two CTAs per SM).  For 3-D grids the tiles that have a
+// compile-time interior kernel come first.  Empty when no such m exists
+// (e.g. one very long dimension): the plain path then takes the grid.
+std::vector<std::vector<int>> rank_m(const Geom &g, int es, int op, int K)
 {
     const int d = g.d;
     const size_t cap = 200 * 1024;
@@ -1167,37 +1186,44 @@ bool choose_m(const Geom &g, int es, int op, int *m_out)
         if (g.l[k] == 0) { lo[k] = hi[k] = 0; continue; }
         lo[k] = std::max(1, g.l[k] - emax_lev);
         hi[k] = std::min(g.l[k], emax_lev);
-        if (lo[k] > hi[k]) return false;
+        if (lo[k] > hi[k]) return {};
     }
-    // 3-D grids: prefer the tiles that have a compile-time interior kernel
-    bool want_t3 = false;
-    if (d == 3) {
-        for (int a = lo[0]; a <= hi[0]; ++a)
-            for (int b = lo[1]; b <= hi[1]; ++b)
-                for (int c = lo[2]; c <= hi[2]; ++c)
-                    want_t3 |= tile3_shape_ok(es, (1 << a) + 1, (1 << b) + 1, (1 << c) + 1);
-    }
+    struct Cand { bool t3; double bytes; std::vector<int> m; };
+    std::vector<Cand> cands;
     for (int k = 0; k < d; ++k) m[k] = lo[k];
-    double best = 1e300;
-    bool found = false;
     for (;;) {
         int64_t vol = 1;
         for (int k = 0; k < d; ++k) vol *= (int64_t)(1 << m[k]) + 1;
-        const bool t3ok = !want_t3 || tile3_shape_ok(es, (1 << m[0]) + 1, (1 << m[1]) + 1, (1 << m[2]) + 1);
-        if (t3ok && (size_t)vol * es <= cap / 2) {
+        if ((size_t)vol * es <= cap / 2) {
             bool ok;
             const double b = estimate_bytes(g, m, es, op, cap, &ok);
-            if (ok && b < best) {
-                best = b;
-                found = true;
-                for (int k = 0; k < d; ++k) m_out[k] = m[k];
+            if (ok) {
+                const bool t3 = d == 3 && tile3_shape_ok(es, (1 << m[0]) + 1, (1 << m[1]) + 1, (1 << m[2]) + 1);
+                cands.push_back(Cand{t3, b, std::vector<int>(m, m + d)});
             }
         }
         int k = 0;
         while (k < d && ++m[k] > hi[k]) { m[k] = lo[k]; ++k; }
         if (k == d) break;
     }
-    return found;
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) {
+        return a.t3 != b.t3 ? a.t3 : a.bytes < b.bytes;
+    });
+    std::vector<std::vector<int>> out;
+    for (const Cand &c : cands) {
+        if ((int)out.size() >= K) break;
+        out.push_back(c.m);
+    }
+    return out;
+}
+
+// The cost model's choice: the first ranked tile.
+bool choose_m(const Geom &g, int es, int op, int *m_out)
+{
+    const auto r = rank_m(g, es, op, 1);
+    if (r.empty()) return false;
+    for (int k = 0; k < g.d; ++k) m_out[k] = r[0][k];
+    return true;
 }
 
 // Class plans for explicit tile exponents m.
@@ -1235,11 +1261,7 @@ bool build_plan(const Geom &g, int es, int op, const int *m_req, Plan *plan)
             if (m_req[k] < 0 || m_req[k] > g.l[k] || (1 << m_req[k]) + 1 > max_extent(es)) return false;
         return build_plan_m(g, es, op, m_req, plan);
     }
-    std::vector<int> key;
-    key.push_back(d);
-    key.push_back(es);
-    key.push_back(op);
-    for (int k = 0; k < d; ++k) key.push_back(g.l[k]);
+    const std::vector<int> key = plan_key(g, es, op);
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         auto it = g_plans.find(key);
@@ -1471,6 +1493,29 @@ bool fused_preferred(const Geom &g, int dtype, int op)
     for (int k = 0; k < g.d; ++k) passes += g.l[k] > 0;
     const double plain = 2.0 * es * (double)g.N * passes;
     return ok && fused < 0.7 * plain;
+}
+
+bool fused_candidates(const Geom &g, int dtype, int op, int K, std::vector<std::vector<int>> *out)
+{
+    if (!fused_supported(g, dtype, op)) return false;
+    *out = rank_m(g, dtype == GBH_F64 ? 8 : 4, op, K);
+    return !out->empty();
+}
+
+bool fused_pin_tiles(const Geom &g, int dtype, int op, const int *m)
+{
+    const int es = dtype == GBH_F64 ? 8 : 4;
+    Plan p;
+    if (!build_plan_m(g, es, op, m, &p)) return false;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[plan_key(g, es, op)] = p;
+    return true;
+}
+
+void fused_forget_pins()
+{
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.clear();
 }
 
 bool fused_tiles(const Geom &g, int dtype, int op, int *m_out)

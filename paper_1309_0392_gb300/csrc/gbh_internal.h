@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "gbh.h"
 
 namespace gbh {
@@ -70,5 +72,20 @@ bool fused_preferred(const Geom &g, int dtype, int op);
 
 // True if the fused path supports this (geometry, dtype, op).
 bool fused_supported(const Geom &g, int dtype, int op);
+
+// Up to K feasible tile-exponent vectors of the fused path, best estimate
+// first (false if the fused path does not take the shape).
+bool fused_candidates(const Geom &g, int dtype, int op, int K, std::vector<std::vector<int>> *out);
+
+// Makes tile exponents m the fused path's choice for this shape (autotuner);
+// fused_forget_pins drops every choice (the cost model decides again).
+bool fused_pin_tiles(const Geom &g, int dtype, int op, const int *m);
+void fused_forget_pins();
+
+// Execution path the autotuner recorded for this shape (gbh_path), or -1.
+int tuned_path(const Geom &g, int dtype, int op);
+
+// Fills n values of dtype at u with scratch values in [-1, 1) (timing data).
+int launch_fill(void *u, int64_t n, int dtype, unsigned seed, cudaStream_t s);
 
 }  // namespace gbh

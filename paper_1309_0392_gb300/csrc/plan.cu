@@ -19,6 +19,8 @@
 // first sweep converts, the last converts back.  Either way hierarchization
 // uses the doubling form 2u - L - R, so it rounds once per stored value.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -1525,6 +1527,11 @@ struct gbh_plan {
     int dev = 0;
     int stall_grid = -1;              // test hook: a dependency nothing releases
     long long spin_limit = kSpinLimit;
+    // execution parameters per op (autotuned or set): resident CTAs per SM
+    // (0 = as many as fit) and the L2 wave of the ticket order
+    int ctas_per_sm[2] = {0, 0};
+    double wave_bytes[2] = {kWaveBytes, kWaveBytes};
+    bool full_scheme = false;         // gbh_plan_create_scheme: the tuned-scheme cache applies
 };
 
 namespace {
@@ -1622,13 +1629,43 @@ int build_items(gbh_plan *p, int op, std::vector<Item> &items, std::vector<int> 
     need.assign((size_t)p->ngrids * kPhases, 0);
     items.clear();
     std::vector<int> order(p->ngrids), wave(p->ngrids), prev(p->ngrids);
-    order_items(p->info.data(), p->ngrids, p->d, p->dtype, op, kItemPoints, kWaveBytes, true, order.data(), wave.data(),
+    order_items(p->info.data(), p->ngrids, p->d, p->dtype, op, kItemPoints, p->wave_bytes[op], true, order.data(), wave.data(),
                 prev.data(), need.data(), [&](const Item &it) {
                     items.push_back(it);
                     return true;
                 });
     return GBH_OK;
 }
+
+// Execution parameters of op (0 CTAs = as many as fit); a new wave reorders
+// the items (the same items, so the device arrays keep their size).
+int set_params(gbh_plan *p, int op, int ctas, double wave)
+{
+    p->ctas_per_sm[op] = ctas;
+    if (wave == p->wave_bytes[op]) return GBH_OK;
+    // the work list is rewritten: no execution of the plan may still read it
+    if (cudaDeviceSynchronize() != cudaSuccess) return GBH_ECUDA;
+    p->wave_bytes[op] = wave;
+    std::vector<Item> items;
+    std::vector<int> need;
+    if (int e = build_items(p, op, items, need)) return e;
+    if (items.size() != p->items[op].size()) return GBH_ECUDA;
+    p->items[op].swap(items);
+    p->need[op].swap(need);
+    if (!p->items[op].empty() &&
+        cudaMemcpy(p->d_items[op], p->items[op].data(), sizeof(Item) * p->items[op].size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return GBH_ECUDA;
+    if (cudaMemcpy(p->d_need[op], p->need[op].data(), sizeof(int) * p->need[op].size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return GBH_ECUDA;
+    return GBH_OK;
+}
+
+// Parameters the autotuner measured for full scheme plans: (d, n, dtype, op)
+// -> (CTAs per SM, wave bytes); new plans of the same scheme start with them.
+std::mutex g_scheme_tune_mu;
+std::map<std::vector<int>, std::pair<int, double>> g_scheme_tuned;
 
 int finish_plan(gbh_plan *p)
 {
@@ -1827,6 +1864,19 @@ int gbh_plan_create_scheme_subset(int d, int n, int dtype, int n_owned, const in
     p->ngrids = (int)p->coeffs.size();
     int e = finish_plan(p);
     if (!e) e = build_sparse(p);
+    p->full_scheme = n_owned < 0;
+    if (!e && p->full_scheme) {
+        for (int op = 0; op < 2 && !e; ++op) {
+            std::pair<int, double> t{0, 0.0};
+            bool have = false;
+            {
+                std::lock_guard<std::mutex> lk(g_scheme_tune_mu);
+                auto it = g_scheme_tuned.find(std::vector<int>{d, n, dtype, op});
+                if (it != g_scheme_tuned.end()) { t = it->second; have = true; }
+            }
+            if (have) e = set_params(p, op, t.first, t.second);
+        }
+    }
     if (e) { free_plan(p); return e; }
     *out = p;
     return GBH_OK;
@@ -1950,6 +2000,7 @@ int gbh_plan_execute(gbh_plan *plan, int op, void *stream)
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem);
         if (per_sm < 1) return GBH_EUNSUPPORTED;
+        if (plan->ctas_per_sm[op] > 0) per_sm = std::min(per_sm, plan->ctas_per_sm[op]);
         const int grid = std::max(1, std::min(num_sms() * per_sm, P.nitems));
         ProfScope ps("batched", s, 2.0 * es * (double)plan->total_points);
         kern<<<grid, kBThreads, smem, s>>>(P);
@@ -2064,6 +2115,132 @@ int gbh_plan_test_stall(gbh_plan *plan, int grid, long long spin_limit)
     if (!plan || grid < -1 || grid >= plan->ngrids || spin_limit < 1) return GBH_EINVAL;
     plan->stall_grid = grid;
     plan->spin_limit = grid < 0 ? kSpinLimit : spin_limit;
+    return GBH_OK;
+}
+
+int gbh_plan_set_params(gbh_plan *plan, int op, int ctas_per_sm, int wave_mb)
+{
+    if (!plan) return GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return GBH_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 32 || wave_mb < 1 || wave_mb > 4096) return GBH_EINVAL;
+    return set_params(plan, op, ctas_per_sm, (double)wave_mb * 1024.0 * 1024.0);
+}
+
+int gbh_plan_get_params(const gbh_plan *plan, int op, int *ctas_per_sm, int *wave_mb)
+{
+    if (!plan || !ctas_per_sm || !wave_mb) return GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return GBH_EINVAL;
+    *ctas_per_sm = plan->ctas_per_sm[op];
+    *wave_mb = (int)(plan->wave_bytes[op] / (1024.0 * 1024.0) + 0.5);
+    return GBH_OK;
+}
+
+int gbh_plan_autotune(gbh_plan *plan, int op, void *stream, gbh_plan_tune_result *out)
+{
+    if (!plan || !out) return GBH_EINVAL;
+    if (op != GBH_HIERARCHIZE && op != GBH_DEHIERARCHIZE) return GBH_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = plan->dtype == GBH_F64 ? 8 : 4;
+    // resident CTAs the kernel allows
+    int maxc = 0;
+    {
+        const size_t smem = kFusedElems * es;
+        auto query = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxc, kern, kBThreads, smem);
+        };
+        if (plan->dtype == GBH_F64) {
+            if (op == OP_H) query(k_fused<double, OP_H>);
+            else query(k_fused<double, OP_D>);
+        } else {
+            if (op == OP_H) query(k_fused<float, OP_H>);
+            else query(k_fused<float, OP_D>);
+        }
+        if (maxc < 1) return GBH_EUNSUPPORTED;
+    }
+    // scratch grids of the plan's shapes, bound in place of the caller's
+    unsigned char *scratch = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&scratch), (size_t)plan->total_points * es) != cudaSuccess)
+        return GBH_ENOMEM;
+    std::vector<void *> saved(plan->h_ptrs, plan->h_ptrs + plan->ngrids);
+    const bool was_bound = plan->bound;
+    std::vector<void *> sp(plan->ngrids);
+    {
+        size_t off = 0;
+        for (int g = 0; g < plan->ngrids; ++g) {
+            sp[g] = scratch + off * es;
+            off += (size_t)plan->info[g].N;
+        }
+    }
+    const int c0 = plan->ctas_per_sm[op];
+    const double w0 = plan->wave_bytes[op];
+    int status = gbh_plan_bind(plan, sp.data(), stream);
+    if (!status) status = launch_fill(scratch, plan->total_points, plan->dtype, 777u, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int other = op == GBH_HIERARCHIZE ? GBH_DEHIERARCHIZE : GBH_HIERARCHIZE;
+    // median of three timed executions of op; the inverse runs between them
+    // (untimed) so that the values keep their magnitude
+    auto time_of = [&](int ctas, double wave, double *ms) -> int {
+        if (int e = set_params(plan, op, ctas, wave)) return e;
+        if (int e = gbh_plan_execute(plan, op, stream)) return e;
+        if (int e = gbh_plan_execute(plan, other, stream)) return e;
+        double t[3];
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            if (int e = gbh_plan_execute(plan, op, stream)) return e;
+            cudaEventRecord(e1, s);
+            if (int e = gbh_plan_execute(plan, other, stream)) return e;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return GBH_ECUDA;
+            float f = 0.f;
+            cudaEventElapsedTime(&f, e0, e1);
+            t[r] = f;
+        }
+        std::sort(t, t + 3);
+        *ms = t[1];
+        return GBH_OK;
+    };
+    double best = 1e300;
+    int bc = 0;
+    double bw = kWaveBytes;
+    const double waves[4] = {8.0, 16.0, 32.0, 64.0};
+    for (int ci = 1; ci <= maxc && !status; ++ci) {
+        for (int wi = 0; wi < 4 && !status; ++wi) {
+            double ms = 0.0;
+            status = time_of(ci, waves[wi] * 1024.0 * 1024.0, &ms);
+            if (status) break;
+            ++out->candidates;
+            if (ms < best) { best = ms; bc = ci; bw = waves[wi] * 1024.0 * 1024.0; }
+            if (ci == maxc && waves[wi] * 1024.0 * 1024.0 == kWaveBytes) out->ms_model = ms;
+        }
+    }
+    if (!status) status = gbh_plan_status(plan, stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the caller's grids again
+    if (was_bound) {
+        const int e = gbh_plan_bind(plan, saved.data(), stream);
+        if (!status) status = e;
+    } else {
+        plan->bound = false;
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (status) {
+        set_params(plan, op, c0, w0);
+        return status;
+    }
+    out->ctas_per_sm = bc;
+    out->wave_mb = (int)(bw / (1024.0 * 1024.0) + 0.5);
+    out->ms_tuned = best;
+    out->max_ctas_per_sm = maxc;
+    if (int e = set_params(plan, op, bc, bw)) return e;
+    if (plan->full_scheme) {
+        std::lock_guard<std::mutex> lk(g_scheme_tune_mu);
+        g_scheme_tuned[std::vector<int>{plan->d, plan->n, plan->dtype, op}] = std::make_pair(bc, bw);
+    }
     return GBH_OK;
 }
 

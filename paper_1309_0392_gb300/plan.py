@@ -130,6 +130,30 @@ class Plan:
         _lib.check(_lib.lib().gbh_plan_scatter(self._h, ctypes.c_void_p(sparse.data_ptr()), 1 if scaled else 0,
                                                ctypes.c_void_p(s.cuda_stream)), "gbh_plan_scatter")
 
+    def set_params(self, op, ctas_per_sm: int, wave_mb: int):
+        """Execution parameters of op: resident CTAs per SM (0 = as many as
+        fit) and the L2 wave of the work queue in MiB."""
+        _lib.check(_lib.lib().gbh_plan_set_params(self._h, int(op), int(ctas_per_sm), int(wave_mb)),
+                   "gbh_plan_set_params")
+
+    def get_params(self, op):
+        c, w = ctypes.c_int(0), ctypes.c_int(0)
+        _lib.check(_lib.lib().gbh_plan_get_params(self._h, int(op), ctypes.byref(c), ctypes.byref(w)),
+                   "gbh_plan_get_params")
+        return int(c.value), int(w.value)
+
+    def autotune(self, op=_lib.GBH_HIERARCHIZE, stream=None):
+        """Times the execution parameters of op on scratch grids and keeps the
+        fastest (gbh_plan_autotune); the bound grids are untouched."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        r = _lib.PlanTuneResult()
+        _lib.check(_lib.lib().gbh_plan_autotune(self._h, int(op), ctypes.c_void_p(s.cuda_stream), ctypes.byref(r)),
+                   "gbh_plan_autotune")
+        return {"ctas_per_sm": int(r.ctas_per_sm), "wave_mb": int(r.wave_mb), "candidates": int(r.candidates),
+                "max_ctas_per_sm": int(r.max_ctas_per_sm), "ms_tuned": float(r.ms_tuned),
+                "ms_model": float(r.ms_model)}
+
     def test_stall(self, grid: int, spin_limit: int = 1 << 14):
         """Failure injection: the grid's work items wait on a dependency that
         is never released (grid=-1 restores normal operation)."""
