@@ -48,6 +48,7 @@ constexpr int kFD = 6;            // dimensions handled by the fused path
 __host__ __device__ constexpr int max_extent(int value_bytes) { return value_bytes == 8 ? 33 : 65; }
 constexpr int kMaxCls = 20;       // classes of one |C| (C(6,3))
 constexpr int kThreads = 256;
+constexpr int64_t kMinClosures = 256;   // closures of an all-lattice class (see make_class)
 
 enum { OP_H = GBH_HIERARCHIZE, OP_D = GBH_DEHIERARCHIZE };
 enum Mode { BLOCK = 0, LATTICE = 1, POINT = 2 };
@@ -521,6 +522,7 @@ struct Tile3Params {
     int64_t N;               // points per grid
     int g0;                  // fixed point: input scale bits
     int growth_bits;         // dehierarchize: bits the block stage may add
+    int pairs;               // 16-byte staging: rows contiguous, strides 1 and 2 odd
 };
 
 template <typename V>
@@ -552,6 +554,11 @@ __device__ __forceinline__ void cp_async4_l2_64(void *smem_dst, const void *gsrc
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global.L2::64B [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -563,8 +570,15 @@ struct kT3Pre { static constexpr int v = OP == GBH_HIERARCHIZE ? 2 : 5; };
 constexpr int kTile3Threads = 320;
 
 // One CTA per closure (the block scheduler overlaps the loads of new closures
-// with the arithmetic of resident ones): every element streams in with
-// cp.async, then three register-pole passes.  LM marks the lattice dimensions
+// with the arithmetic of resident ones): the closure streams in with
+// cp.async, then three register-pole passes.  fp64 closures whose rows are
+// contiguous and whose row strides along dimensions 1 and 2 are odd (every
+// grid with 2^l + 1 points per dimension, outside the lattice classes) stage
+// in 16-byte copies: consecutive closure rows alternate in the parity of
+// their global element offset exactly as they do in a dense shared-memory
+// layout of odd pitch E0, so shifting the layout by the parity of the first
+// row aligns every row's 16-byte pairs in both memories; each row is one
+// 8-byte copy and (E0 - 1) / 2 16-byte copies.  LM marks the lattice dimensions
 // of the class (bit k: dimension k is on the block lattice; 0 is the interior
 // class): a lattice dimension takes global strides 2^{m_k} S_k, has no group
 // index, and its whole extent is written.
@@ -579,7 +593,7 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     constexpr int B0 = E0 - 1, B1 = E1 - 1, B2 = E2 - 1;
     constexpr int NBLOCK = (L0 ? 0 : 1) + (L1 ? 0 : 1) + (L2 ? 0 : 1);
     extern __shared__ __align__(16) unsigned char sm[];
-    V *vals = reinterpret_cast<V *>(sm);
+    V *vals = reinterpret_cast<V *>(sm);     // shifted by one value below (16-byte staging)
     __shared__ int s_emax;
     __shared__ unsigned long long s_or;
     const int tid = threadIdx.x;
@@ -600,6 +614,32 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
     // tile-relative offsets in 32 bits (the host checks that the closure's
     // span fits)
     const int g0s = (int)P.gs0, g1s = (int)P.gs1, g2s = (int)P.gs2;
+    constexpr bool V16 = sizeof(ST) == 8 && !L0 && (E0 & 1);
+    if (V16 && P.pairs) {
+        // row r = y + E1 z starts at global parity o = o00 ^ (r & 1) and at
+        // shared parity (E0 r + o00) & 1, the same; copy c of row r is
+        // element 0 alone (o = 1) or element E0 - 1 alone (o = 0) for c = 0,
+        // else the pair starting at element 2c - 1 (o = 1) or 2c - 2 (o = 0)
+        const int o00 = (int)(((unsigned long long)(uintptr_t)ub >> 3) & 1ull);
+        vals += o00;
+        constexpr int CH = (E0 + 1) / 2, RW = T / CH;
+        if (tid < CH * RW) {
+            const int c = tid % CH;
+            for (int r = tid / CH; r < R; r += RW) {
+                const int y = r % E1, z = r / E1;
+                const int o = o00 ^ (r & 1);
+                const ST *src = ub + (y * g1s + z * g2s);
+                V *dst = vals + r * E0;
+                if (c == 0) {
+                    const int x = o ? 0 : E0 - 1;
+                    cp_async8(dst + x, src + x);
+                } else {
+                    const int x = 2 * c - 2 + o;
+                    cp_async16(dst + x, src + x);
+                }
+            }
+        }
+    } else {
     for (int e = tid; e < NV; e += T) {
         const int x = e % E0, r = e / E0;
         const ST *src = ub + (x * g0s + (r % E1) * g1s + (r / E1) * g2s);
@@ -610,6 +650,7 @@ __global__ void __launch_bounds__(kTile3Threads, 2) k_tile3(const __grid_constan
             if constexpr (sizeof(ST) == 8) cp_async8(vals + e, src);
             else cp_async4(vals + e, src);
         }
+    }
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -1065,15 +1106,29 @@ bool make_class(const Geom &g, const int *m, unsigned mask, int es, size_t cap, 
         for (int k = 1; k < d; ++k) v *= (c.mode[k] == BLOCK ? c.e[k] - 2 : c.e[k]);
         return v;
     };
+    auto closures = [&]() {
+        int64_t v = 1;
+        for (int k = 0; k < d; ++k) v *= c.ngrp[k];
+        return v;
+    };
+    // a class with every dimension on the lattice has one closure, which would
+    // leave all SMs but one idle: its lattice dimensions become point
+    // dimensions until it has kMinClosures closures
+    bool all_lattice = true;
+    for (int k = 0; k < d; ++k) all_lattice &= c.mode[k] != BLOCK;
     for (;;) {
         c.V = (int)std::min<int64_t>(volume(), INT32_MAX);
         c.rows = c.V / c.e[0];
         c.wrows = (int)std::min<int64_t>(wvolume(), INT32_MAX);
-        if (closure_smem(c, es) <= cap) break;
+        const bool fits = closure_smem(c, es) <= cap;
+        if (fits && (!all_lattice || closures() >= kMinClosures)) break;
         int best = -1;
         for (int k = 0; k < d; ++k)
-            if (c.mode[k] == LATTICE && (best < 0 || c.e[k] > c.e[best])) best = k;
-        if (best < 0) return false;                     // block closure alone too big
+            if (c.mode[k] == LATTICE && (fits ? c.e[k] > 2 : true) && (best < 0 || c.e[k] > c.e[best])) best = k;
+        if (best < 0) {
+            if (fits) break;
+            return false;                               // block closure alone too big
+        }
         to_point(best);
     }
     int ss = 1;
@@ -1342,7 +1397,8 @@ bool tile3_shape_ok(int es, int E0, int E1, int E2)
 template <typename ST, bool FIX, int OP, int E0, int E1, int E2, int LM>
 int launch_tile3_shape(const Tile3Params &P, ST *u, cudaStream_t st, double alg_bytes, const char *name)
 {
-    constexpr size_t smem = (size_t)E0 * E1 * E2 * sizeof(ST);
+    // one spare value: the 16-byte staging shifts the closure by one value
+    constexpr size_t smem = ((size_t)E0 * E1 * E2 + 1) * sizeof(ST);
     auto kern = k_tile3<ST, FIX, OP, E0, E1, E2, LM>;
     static bool attr = false;
     if (!attr) {
@@ -1392,6 +1448,7 @@ int launch_tile3(const Plan &pl, const ClassPlan &cp, const Geom &g, ST *u, cuda
     P.N = g.N;
     P.g0 = c.g0;
     P.growth_bits = c.growth_bits;
+    P.pairs = c.gstride[0] == 1 && (c.gstride[1] & 1) && (c.gstride[2] & 1) && (c.e[0] & 1);
     const double bytes = 2.0 * sizeof(ST) * (double)P.total * c.W;
     const char *name = cp.mask == 0 ? "fused_class0" : cp.mask == 1 ? "fused_class1_d0" : cp.mask == 2 ? "fused_class1_d1" : "fused_class1_d2";
 #define GBH_T3_CALL(a, b, cc, m) \
