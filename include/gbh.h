@@ -334,8 +334,7 @@ int gbh_sparse_index_of_grid(int d, int n, const int32_t *levels, int64_t *out);
  * fp32 tolerance.  Returns
  * GBH_ERANGE when the grids need more work items than the array holds
  * (roughly 80,000 items of 65,536 points).  The first call on a device looks
- * up the array's device address; make that call before any stream capture.
- * Every call rewrites the shared array and clears its counters: calls whose
+ * up the array's device address.  Every call rewrites the shared array and clears its counters: calls whose
  * kernels overlap on the GPU (other streams, other threads) race, so order
  * them on one stream.  Not thread-safe on the host.  The return code covers
  * argument and launch errors only; a bounded device-side wait that gives up

@@ -2272,8 +2272,8 @@ int gbh_plan_status(gbh_plan *plan, void *stream)
 // cudaMalloc at all at that point.  The work queue, its counters and the
 // per-grid tables live in one file-scope device array of fixed size instead of
 // in a plan; the kernel is the plan's k_batched.  The array's device address
-// is looked up once per device (the first call on a device does this, so that
-// call should come before any stream capture).  Every call shares the array
+// is looked up once per device (by the first call on that device).  Every
+// call shares the array
 // and rewrites it: calls that overlap on the GPU race; the counters are
 // cleared by every call.  The first 256 bytes hold a status word that no call
 // clears: a bounded wait that gives up sets it to GBH_ETIMEOUT, and
