@@ -608,8 +608,8 @@ def run_ours(args):
 
 
 def run_case(args):
-    """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith]]`
-    (path auto/plain/fused/grouped, arith 0/1/2), `scheme:d,n:op:dtype` or
+    """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith[:variant]]]`
+    (path auto/plain/fused/grouped, arith 0/1/2, variant 0/1/2 of the fused path), `scheme:d,n:op:dtype` or
     `gather:d,n:op:dtype` (the scheme's gather into the sparse grid) (op h/d/a,
     dtype f64/f32), run warmup + steps times; prints one JSON line with the
     median time and the per-kernel launch times of a second, profiled pass."""
@@ -621,6 +621,7 @@ def run_case(args):
     path = {"auto": gbh.GBH_PATH_AUTO, "plain": gbh.GBH_PATH_PLAIN, "fused": gbh.GBH_PATH_FUSED,
             "grouped": gbh.GBH_PATH_GROUPED}[extra[0] if extra else "auto"]
     arith = int(extra[1]) if len(extra) > 1 else 0
+    variant = int(extra[2]) if len(extra) > 2 else 0
     dtype = torch.float64 if dt == "f64" else torch.float32
     opc = {"h": gbh.GBH_HIERARCHIZE, "d": gbh.GBH_DEHIERARCHIZE, "a": gbh.GBH_ADJOINT,
            "t": gbh.GBH_DEHIERARCHIZE_ADJOINT}[op]
@@ -628,7 +629,7 @@ def run_case(args):
     if kind == "transform":
         levels = tuple(int(v) for v in spec.split(","))
         t = torch.empty(gbh.num_points(levels), dtype=dtype, device="cuda").uniform_(-1, 1, generator=gen)
-        fn = lambda: gbh.transform(t, levels, opc, path=path, arith=arith)  # noqa: E731
+        fn = lambda: gbh.transform(t, levels, opc, path=path, arith=arith, variant=variant)  # noqa: E731
         pts = t.numel()
     else:
         d, n = (int(v) for v in spec.split(","))

@@ -42,10 +42,12 @@ def _stream_ptr(t, stream):
 
 
 def transform(t, levels, op=GBH_HIERARCHIZE, *, path=GBH_PATH_AUTO, tile=None, arith=0,
-              stream=None, batch=None):
+              variant=0, stream=None, batch=None):
     """In-place transform of grid tensor ``t`` (op: GBH_HIERARCHIZE,
     GBH_DEHIERARCHIZE, GBH_ADJOINT or GBH_DEHIERARCHIZE_ADJOINT).  With
     ``batch=B`` the tensor holds B grids of the level vector back to back.
+    ``variant`` picks the fused path's kernels for 3-D fp64 tiles (5,4,4):
+    0 the interior class on its own kernel, 1 the generic tile kernels.
     Returns ``t``."""
     B = 1 if batch is None else int(batch)
     if B < 1:
@@ -60,6 +62,7 @@ def transform(t, levels, op=GBH_HIERARCHIZE, *, path=GBH_PATH_AUTO, tile=None, a
     opt = _lib.Options()
     opt.path = int(path)
     opt.arith = int(arith)
+    opt.variant = int(variant)
     if tile is not None:
         for k, m in enumerate(tile):
             opt.tile_exp[k] = int(m)

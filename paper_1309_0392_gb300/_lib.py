@@ -44,7 +44,7 @@ class PlanTuneResult(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("tile_exp", ctypes.c_int32 * 16),
-                ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("arith", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _I32P = ctypes.POINTER(ctypes.c_int32)

@@ -1496,8 +1496,11 @@ int launch_lattice(const Plan &pl, const ClassPlan &cp, int k, const Geom &g, ST
     return check_launch();
 }
 
+// Kernel variants of a plan (gbh_options.variant): 0 the interior-class
+// kernel of interior3.cu where it takes the tile, 1 the generic tile kernels
+// only.
 template <typename ST, bool FIX, int OP>
-int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
+int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st, bool int3)
 {
     const int d = pl.d;
     auto closure = [&](int c) -> int {
@@ -1505,6 +1508,13 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st)
         // classes with a compile-time kernel go one by one, the rest together
         std::vector<ClassPlan> rest;
         for (const ClassPlan &cp : pl.by_size[c]) {
+            if (int3 && cp.mask == 0u) {
+                const int r = interior3_transform(reinterpret_cast<double *>(u), g, pl.m, OP, st);
+                if (r != 1) {
+                    if (r != GBH_OK) return r;
+                    continue;
+                }
+            }
             const int r = launch_tile3<ST, FIX, OP>(pl, cp, g, u, st);
             if (r == 1) rest.push_back(cp);
             else if (r != GBH_OK) return r;
@@ -1594,12 +1604,13 @@ int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_opti
     if (dtype == GBH_F64) {
         double *u = static_cast<double *>(data);
         const bool fix = arith != 1;
-        if (op == OP_H) return fix ? run_plan<double, true, OP_H>(pl, g, u, s) : run_plan<double, false, OP_H>(pl, g, u, s);
-        return fix ? run_plan<double, true, OP_D>(pl, g, u, s) : run_plan<double, false, OP_D>(pl, g, u, s);
+        const bool int3 = fix && !(opt && opt->variant == 1);
+        if (op == OP_H) return fix ? run_plan<double, true, OP_H>(pl, g, u, s, int3) : run_plan<double, false, OP_H>(pl, g, u, s, false);
+        return fix ? run_plan<double, true, OP_D>(pl, g, u, s, int3) : run_plan<double, false, OP_D>(pl, g, u, s, false);
     }
     float *u = static_cast<float *>(data);
-    if (op == OP_H) return run_plan<float, false, OP_H>(pl, g, u, s);
-    return run_plan<float, false, OP_D>(pl, g, u, s);
+    if (op == OP_H) return run_plan<float, false, OP_H>(pl, g, u, s, false);
+    return run_plan<float, false, OP_D>(pl, g, u, s, false);
 }
 
 }  // namespace gbh

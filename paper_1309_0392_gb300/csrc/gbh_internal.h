@@ -63,6 +63,12 @@ int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s
 int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,
                     cudaStream_t s);
 
+// Interior class of the fused path for 3-D fp64 grids in fixed point with
+// tile exponents (5,4,4), one closure per CTA (interior3.cu).  Returns 1
+// (nothing launched) when the shape is not one it takes.
+bool interior3_applicable(const Geom &g, const int *m);
+int interior3_transform(double *u, const Geom &g, const int *m, int op, cudaStream_t s);
+
 // Tile exponents the fused path would choose (false if unsupported).
 bool fused_tiles(const Geom &g, int dtype, int op, int *m_out);
 
