@@ -609,7 +609,7 @@ def run_ours(args):
 
 def run_case(args):
     """One small workload for profilers: `transform:L0,L1,..:op:dtype[:path[:arith[:variant]]]`
-    (path auto/plain/fused/grouped, arith 0/1/2, variant 0/1/2 of the fused path), `scheme:d,n:op:dtype` or
+    (path auto/plain/fused/grouped, arith 0/1/2, variant 0/1: the kernel choice within the path), `scheme:d,n:op:dtype` or
     `gather:d,n:op:dtype` (the scheme's gather into the sparse grid) (op h/d/a,
     dtype f64/f32), run warmup + steps times; prints one JSON line with the
     median time and the per-kernel launch times of a second, profiled pass."""

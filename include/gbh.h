@@ -130,10 +130,15 @@ typedef struct {
                               on GBH_PATH_PLAIN, int64 block fixed point on the
                               others), 1 = native fp64, 2 = int64 block fixed
                               point (one binary scale per tile or pole group)    */
-    int32_t variant;       /* fused path, 3-D fp64 fixed point with tile
-                              exponents (5,4,4): 0 = the interior class on its
-                              own kernel (default), 1 = the generic tile
-                              kernel for every class                            */
+    int32_t variant;       /* kernel choice within a path, same results
+                              within the stated tolerance.  Fused path, 3-D
+                              fp64 fixed point with tile exponents (5,4,4):
+                              0 = the interior class on its own kernel
+                              (default), 1 = the generic tile kernel for every
+                              class.  Plain path with native arithmetic:
+                              0 = two consecutive dimensions per pass where
+                              their poles fit a pair tile (default; results
+                              bit-identical to 1), 1 = one pass per dimension */
     int32_t reserved[5];
 } gbh_options;
 

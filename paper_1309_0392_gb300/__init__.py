@@ -46,8 +46,11 @@ def transform(t, levels, op=GBH_HIERARCHIZE, *, path=GBH_PATH_AUTO, tile=None, a
     """In-place transform of grid tensor ``t`` (op: GBH_HIERARCHIZE,
     GBH_DEHIERARCHIZE, GBH_ADJOINT or GBH_DEHIERARCHIZE_ADJOINT).  With
     ``batch=B`` the tensor holds B grids of the level vector back to back.
-    ``variant`` picks the fused path's kernels for 3-D fp64 tiles (5,4,4):
-    0 the interior class on its own kernel, 1 the generic tile kernels.
+    ``variant`` picks kernels within a path (same results within the
+    stated tolerance): fused path, 3-D fp64 tiles (5,4,4): 0 the interior
+    class on its own kernel, 1 the generic tile kernels; plain path with
+    native arithmetic: 0 two consecutive dimensions per pass where they fit
+    a pair tile, 1 one pass per dimension (bit-identical results).
     Returns ``t``."""
     B = 1 if batch is None else int(batch)
     if B < 1:

@@ -182,7 +182,8 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     if (path != GBH_PATH_AUTO && path != GBH_PATH_PLAIN && path != GBH_PATH_FUSED && path != GBH_PATH_GROUPED)
         return GBH_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (path == GBH_PATH_PLAIN) return plain_transform(data, g, dtype, op, s, opt && opt->arith == 2);
+    const bool pairs = !(opt && opt->variant == 1);
+    if (path == GBH_PATH_PLAIN) return plain_transform(data, g, dtype, op, s, opt && opt->arith == 2, pairs);
     if (path == GBH_PATH_FUSED) {
         if (!fused_supported(g, dtype, op)) return GBH_EUNSUPPORTED;
         return fused_transform(data, g, dtype, op, opt, s);
@@ -197,7 +198,7 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     if (tp != GBH_PATH_PLAIN && g.N >= 4096 && fused_preferred(g, dtype, op))
         return fused_transform(data, g, dtype, op, opt, s);
     // fp64 sweeps compute in fixed point unless native arithmetic is asked for
-    return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1));
+    return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1), pairs);
 }
 
 int gbh_hierarchize(void *data, int d, const int32_t *levels, int dtype, void *stream)

@@ -56,8 +56,11 @@ int grouped_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t
 
 // Plain path: one sweep per dimension.  fixed64: fp64 pole groups compute in
 // int64 fixed point (otherwise native arithmetic in the serial operation
-// order, bit-identical to the serial algorithm).
-int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64 = false);
+// order, bit-identical to the serial algorithm).  pairs: with native
+// arithmetic, two consecutive dimensions per pass where their poles fit a
+// pair tile (same results, one memory crossing fewer per pair).
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64 = false,
+                    bool pairs = true);
 
 // Fused path: dyadic tiles (class-ordered), see fused.cu.
 int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,

@@ -411,6 +411,167 @@ __global__ void __launch_bounds__(256) k_pole_group(T *__restrict__ u, int64_t S
 }
 
 // ---------------------------------------------------------------------------
+// pair kernel: dimensions a and a+1 in one pass (native arithmetic)
+// ---------------------------------------------------------------------------
+//
+// A CTA stages a tile that holds whole poles of both dimensions, sweeps
+// dimension a and then dimension a+1 in shared memory (one thread per pole,
+// the pole held in registers as in the pole kernel) and stores the tile back:
+// one crossing of memory for two dimensions.  Every point receives the same
+// operations in the same order as from two single-dimension sweeps, so the
+// results are bit-identical to them.
+//   a = 0   (ROWS) Q consecutive planes of n0 x n1 points: one contiguous
+//           range, copied in 16-byte pieces (the range's first element sits
+//           at the shared-memory offset that makes both sides aligned).
+//   a >= 1  B consecutive positions j of the dimensions below a (a run of B
+//           elements at every (i_a, i_{a+1})), B a power of two, for one
+//           index o of the dimensions above a+1; shared index jj + B r with
+//           r = i_a + n_a i_{a+1}.  Neighbouring threads own neighbouring
+//           poles, so the strided pole reads are free of bank conflicts.
+constexpr int kPairThreads = 256;
+constexpr int kPairBytes = 104 * 1024;   // two CTAs per SM
+
+template <typename T>
+__host__ __device__ constexpr int pair_max_level()
+{
+    return sizeof(T) == 4 ? 6 : 5;       // pole of 65 (fp32) or 33 (fp64) in registers
+}
+
+__device__ __forceinline__ void lds_val(float &v, unsigned a)
+{
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+}
+__device__ __forceinline__ void lds_val(double &v, unsigned a)
+{
+    asm volatile("ld.shared.f64 %0, [%1];\n" : "=d"(v) : "r"(a));
+}
+__device__ __forceinline__ void sts_val(unsigned a, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;\n" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts_val(unsigned a, double v)
+{
+    asm volatile("st.shared.f64 [%0], %1;\n" ::"r"(a), "d"(v) : "memory");
+}
+
+// One pole of 2^L + 1 points at shared address a, stride st bytes: loaded
+// into registers, transformed, stored.  The store addresses start from an
+// opaque copy of a, so that they are recomputed rather than kept live from
+// the loads (which would hold one register per point).
+template <typename T, int OP, int L>
+__device__ __forceinline__ void pole_via_regs(unsigned a, unsigned st)
+{
+    constexpr int n = (1 << L) + 1;
+    T v[n];
+#pragma unroll
+    for (int i = 0; i < n; ++i) lds_val(v[i], a + i * st);
+    transform_regs<T, OP, L>(v);
+    unsigned b;
+    asm volatile("mov.b32 %0, %1;\n" : "=r"(b) : "r"(a));
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+        if (OP == OP_A || OP == OP_DT || (i > 0 && i < n - 1)) sts_val(b + i * st, v[i]);
+}
+
+// pole at p (shared memory), stride st elements, level l
+template <typename T, int OP>
+__device__ __forceinline__ void pole_shared(T *p, int st, int l)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p), sb = (unsigned)(st * (int)sizeof(T));
+    switch (l) {
+        case 1: pole_via_regs<T, OP, 1>(a, sb); break;
+        case 2: pole_via_regs<T, OP, 2>(a, sb); break;
+        case 3: pole_via_regs<T, OP, 3>(a, sb); break;
+        case 4: pole_via_regs<T, OP, 4>(a, sb); break;
+        case 5: pole_via_regs<T, OP, 5>(a, sb); break;
+        default:
+            if constexpr (pair_max_level<T>() >= 6) pole_via_regs<T, OP, 6>(a, sb);
+            break;
+    }
+}
+
+__device__ __forceinline__ void pg_cp16(void *smem_dst, const void *gsrc)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void pg_cp(T *smem_dst, const T *gsrc)
+{
+    if constexpr (sizeof(T) == 8) pg_cp8(smem_dst, gsrc);
+    else pg_cp4(smem_dst, gsrc);
+}
+
+// ROWS: units = planes, Q planes per CTA.  Otherwise units = bundles of Q
+// positions (bpo per index o), Sa = stride of dimension a.
+template <typename T, int OP, bool ROWS>
+__global__ void __launch_bounds__(kPairThreads, 2)
+k_pair(T *__restrict__ u, int64_t units, int64_t Sa, int64_t bpo, int la, int lb, int Q)
+{
+    extern __shared__ __align__(16) unsigned char smr[];
+    T *sv = reinterpret_cast<T *>(smr);
+    const int na = (1 << la) + 1, nb = (1 << lb) + 1, M = na * nb;
+    const int tid = threadIdx.x;
+    if constexpr (ROWS) {
+        constexpr int VEC = 16 / sizeof(T);
+        const int64_t p0 = (int64_t)blockIdx.x * Q;
+        const int Qc = (int)((units - p0) < (int64_t)Q ? (units - p0) : (int64_t)Q);
+        const int cnt = Qc * M;
+        T *g = u + p0 * M;
+        const int mis = (int)((reinterpret_cast<uintptr_t>(g) / sizeof(T)) & (VEC - 1));
+        const int head = min(cnt, (VEC - mis) & (VEC - 1));
+        const int body = (cnt - head) / VEC;
+        const int tail = head + body * VEC;
+        T *s = sv + mis;    // element e of the range at s[e]; s + head is 16-byte aligned
+        for (int e = tid; e < head; e += kPairThreads) pg_cp(s + e, g + e);
+        for (int c = tid; c < body; c += kPairThreads) pg_cp16(s + head + c * VEC, g + head + c * VEC);
+        for (int e = tail + tid; e < cnt; e += kPairThreads) pg_cp(s + e, g + e);
+        pg_commit_wait();
+        __syncthreads();
+        for (int q = tid; q < Qc * nb; q += kPairThreads) pole_shared<T, OP>(s + q * na, 1, la);
+        __syncthreads();
+        for (int q = tid; q < Qc * na; q += kPairThreads) {
+            const int p = q / na, ia = q - p * na;
+            pole_shared<T, OP>(s + p * M + ia, na, lb);
+        }
+        __syncthreads();
+        for (int e = tid; e < head; e += kPairThreads) g[e] = s[e];
+        for (int c = tid; c < body; c += kPairThreads)
+            *reinterpret_cast<uint4 *>(g + head + c * VEC) = *reinterpret_cast<const uint4 *>(s + head + c * VEC);
+        for (int e = tail + tid; e < cnt; e += kPairThreads) g[e] = s[e];
+    } else {
+        const int64_t o = (int64_t)blockIdx.x / bpo;
+        const int64_t j0 = ((int64_t)blockIdx.x - o * bpo) * Q;
+        const int Bc = (int)((Sa - j0) < (int64_t)Q ? (Sa - j0) : (int64_t)Q);
+        T *g = u + o * Sa * M + j0;
+        const int lgB = __ffs(Q) - 1;
+        const int cnt = Q * M;
+        // Q divides the block size: a thread keeps its jj, r steps by kPairThreads / Q
+        const int jj = tid & (Q - 1);
+        const int rstep = kPairThreads >> lgB;
+        if (jj < Bc)
+            for (int w = tid, r = tid >> lgB; w < cnt; w += kPairThreads, r += rstep)
+                pg_cp(sv + w, g + jj + Sa * r);
+        pg_commit_wait();
+        __syncthreads();
+        for (int q = tid; q < Q * nb; q += kPairThreads) {
+            const int ib = q >> lgB;
+            if (jj < Bc) pole_shared<T, OP>(sv + ib * na * Q + jj, Q, la);
+        }
+        __syncthreads();
+        for (int q = tid; q < Q * na; q += kPairThreads) {
+            const int ia = q >> lgB;
+            if (jj < Bc) pole_shared<T, OP>(sv + ia * Q + jj, na * Q, lb);
+        }
+        __syncthreads();
+        if (jj < Bc)
+            for (int w = tid, r = tid >> lgB; w < cnt; w += kPairThreads, r += rstep)
+                g[jj + Sa * r] = sv[w];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
 
@@ -567,34 +728,98 @@ int sweep_dim(T *u, const Geom &g, int k, cudaStream_t st, bool fixed)
     return check_launch();
 }
 
-template <typename T, int OP>
-int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed)
+// Tile of the pair pass over dimensions (k, k+1): planes per CTA (k = 0) or
+// bundle width B (k >= 1); 0 when the pair does not fit (a pole longer than
+// the register pole, a tile over the shared-memory budget, or fewer than 8
+// positions below k, which would leave the runs of a bundle uncoalesced).
+template <typename T>
+int pair_tile(const Geom &g, int k)
 {
+    if (k + 1 >= g.d) return 0;
+    const int la = g.l[k], lb = g.l[k + 1];
+    if (la < 1 || lb < 1 || la > pair_max_level<T>() || lb > pair_max_level<T>()) return 0;
+    const int64_t M = g.n[k] * g.n[k + 1];
+    const int64_t cap = kPairBytes / (int64_t)sizeof(T);
+    if (k == 0) {
+        const int64_t Q = (cap - 16 / (int64_t)sizeof(T)) / M;
+        return Q >= 1 ? (int)std::min<int64_t>(Q, 256) : 0;
+    }
+    int64_t B = 128;
+    while (B > 8 && (B * M > cap || B > g.S[k])) B >>= 1;
+    return (B * M <= cap && B <= g.S[k]) ? (int)B : 0;
+}
+
+template <typename T, int OP>
+int launch_pair(T *u, const Geom &g, int k, int Q, cudaStream_t st)
+{
+    const int la = g.l[k], lb = g.l[k + 1];
+    const int64_t M = g.n[k] * g.n[k + 1];
+    static bool attr[2] = {false, false};
+    const bool rows = k == 0;
+    if (!attr[rows]) {
+        if (rows) cudaFuncSetAttribute(k_pair<T, OP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairBytes + 16);
+        else cudaFuncSetAttribute(k_pair<T, OP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairBytes + 16);
+        attr[rows] = true;
+    }
+    ProfScope ps("plain_pair", st, 2.0 * sizeof(T) * (double)g.total);
+    if (rows) {
+        const int64_t planes = g.total / M;
+        const int64_t blocks = (planes + Q - 1) / Q;
+        if (blocks > INT32_MAX) return GBH_ERANGE;
+        const size_t smem = ((size_t)Q * M + 16 / sizeof(T)) * sizeof(T);
+        k_pair<T, OP, true><<<(unsigned)blocks, kPairThreads, smem, st>>>(u, planes, 1, 1, la, lb, Q);
+    } else {
+        const int64_t Sa = g.S[k];
+        const int64_t outer = g.total / (Sa * M);
+        const int64_t bpo = (Sa + Q - 1) / Q;
+        if (outer * bpo > INT32_MAX) return GBH_ERANGE;
+        const size_t smem = (size_t)Q * M * sizeof(T);
+        k_pair<T, OP, false><<<(unsigned)(outer * bpo), kPairThreads, smem, st>>>(u, outer * bpo, Sa, bpo, la, lb, Q);
+    }
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+// pairs: two consecutive dimensions per pass where they fit a pair tile
+// (native arithmetic only)
+template <typename T, int OP>
+int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed, bool pairs)
+{
+    constexpr bool kFixable = sizeof(T) == 8 && OP != OP_DT;
+    const bool native = !(kFixable && fixed);
     for (int k = 0; k < g.d; ++k) {
         if (g.l[k] == 0) continue;
+        if (pairs && native) {
+            if (const int Q = pair_tile<T>(g, k)) {
+                if (int e = launch_pair<T, OP>(u, g, k, Q, st)) return e;
+                ++k;
+                continue;
+            }
+        }
         if (int e = sweep_dim<T, OP>(u, g, k, st, fixed)) return e;
     }
     return GBH_OK;
 }
 
 template <typename T>
-int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed)
+int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed, bool pairs)
 {
     switch (op) {
-        case OP_H: return plain_all<T, OP_H>(u, g, st, fixed);
-        case OP_D: return plain_all<T, OP_D>(u, g, st, fixed);
-        case OP_A: return plain_all<T, OP_A>(u, g, st, fixed);
-        case OP_DT: return plain_all<T, OP_DT>(u, g, st, false);
+        case OP_H: return plain_all<T, OP_H>(u, g, st, fixed, pairs);
+        case OP_D: return plain_all<T, OP_D>(u, g, st, fixed, pairs);
+        case OP_A: return plain_all<T, OP_A>(u, g, st, fixed, pairs);
+        case OP_DT: return plain_all<T, OP_DT>(u, g, st, false, pairs);
         default: return GBH_EINVAL;
     }
 }
 
 }  // namespace
 
-int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64)
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64, bool pairs)
 {
-    if (dtype == GBH_F64) return plain_dispatch<double>(static_cast<double *>(data), g, op, s, fixed64);
-    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s, false);
+    if (dtype == GBH_F64) return plain_dispatch<double>(static_cast<double *>(data), g, op, s, fixed64, pairs);
+    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s, false, pairs);
     return GBH_EDTYPE;
 }
 
