@@ -571,6 +571,98 @@ k_pair(T *__restrict__ u, int64_t units, int64_t Sa, int64_t bpo, int la, int lb
     }
 }
 
+// Square pairs of outer dimensions (a >= 1, l_a = l_b = L <= 5): no staging
+// copy.  A CTA owns B = 64 / sizeof(T) consecutive positions j (runs of 64
+// bytes) and n = 2^L + 1 threads per position.  Thread (jj, q) loads the pole
+// of dimension a at i_{a+1} = q straight from global memory into registers
+// (a warp reads whole runs: coalesced), transforms it and parks it in shared
+// memory; after one barrier it takes the pole of dimension a+1 at i_a = q
+// from shared memory, transforms it and stores it to global memory.  Shared
+// memory serves only the exchange between the two dimensions (one store and
+// one load per point), and every thread keeps a whole pole of loads in
+// flight.  Shared index (i_{a+1} n + i_a) B + jj: the two positions of q in
+// a warp fall on opposite bank halves in both phases.
+template <typename T>
+__host__ __device__ constexpr int square_run()
+{
+    return 64 / (int)sizeof(T);
+}
+
+template <typename T, int OP, int L>
+__global__ void __launch_bounds__(square_run<T>() * ((1 << L) + 1), 2)
+k_pair_square(T *__restrict__ u, int64_t Sa, int64_t bpo)
+{
+    constexpr int n = (1 << L) + 1, B = square_run<T>();
+    extern __shared__ __align__(16) unsigned char smr[];
+    T *sv = reinterpret_cast<T *>(smr);
+    const int tid = threadIdx.x;
+    const int jj = tid & (B - 1), q = tid / B;
+    const int64_t o = (int64_t)blockIdx.x / bpo;
+    const int64_t j0 = ((int64_t)blockIdx.x - o * bpo) * B;
+    const bool act = j0 + jj < Sa;
+    T *g = u + o * Sa * n * n + j0 + jj;
+    T v[n];
+    if (act) {
+        const T *p = g + Sa * n * q;            // pole of dimension a at i_{a+1} = q
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = p[Sa * i];
+        transform_regs<T, OP, L>(v);
+#pragma unroll
+        for (int i = 0; i < n; ++i) sv[(q * n + i) * B + jj] = v[i];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) v[i] = sv[(i * n + q) * B + jj];
+        transform_regs<T, OP, L>(v);
+        T *p = g + Sa * q;                      // pole of dimension a+1 at i_a = q
+#pragma unroll
+        for (int i = 0; i < n; ++i) p[Sa * n * i] = v[i];
+    }
+}
+
+template <typename T, int OP, int L>
+int launch_pair_square(T *u, const Geom &g, int k, cudaStream_t st)
+{
+    constexpr int n = (1 << L) + 1, B = square_run<T>();
+    const int64_t Sa = g.S[k];
+    const int64_t bpo = (Sa + B - 1) / B;
+    const int64_t blocks = g.total / (Sa * n * n) * bpo;
+    if (blocks > INT32_MAX) return GBH_ERANGE;
+    const size_t smem = (size_t)B * n * n * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_pair_square<T, OP, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    ProfScope ps("plain_pair_square", st, 2.0 * sizeof(T) * (double)g.total);
+    k_pair_square<T, OP, L><<<(unsigned)blocks, B * n, smem, st>>>(u, Sa, bpo);
+    ps.done();
+    count_launches(1);
+    return check_launch();
+}
+
+// the square kernel takes the pair (k, k+1) when k >= 1, l_k = l_{k+1} in
+// [1, 5] and at least one run of positions lies below k
+template <typename T>
+bool pair_square_fits(const Geom &g, int k)
+{
+    return k >= 1 && k + 1 < g.d && g.l[k] == g.l[k + 1] && g.l[k] >= 1 && g.l[k] <= 5 &&
+           g.S[k] >= square_run<T>();
+}
+
+template <typename T, int OP>
+int launch_pair_square_any(T *u, const Geom &g, int k, cudaStream_t st)
+{
+    switch (g.l[k]) {
+        case 1: return launch_pair_square<T, OP, 1>(u, g, k, st);
+        case 2: return launch_pair_square<T, OP, 2>(u, g, k, st);
+        case 3: return launch_pair_square<T, OP, 3>(u, g, k, st);
+        case 4: return launch_pair_square<T, OP, 4>(u, g, k, st);
+        default: return launch_pair_square<T, OP, 5>(u, g, k, st);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
@@ -761,7 +853,7 @@ int launch_pair(T *u, const Geom &g, int k, int Q, cudaStream_t st)
         else cudaFuncSetAttribute(k_pair<T, OP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairBytes + 16);
         attr[rows] = true;
     }
-    ProfScope ps("plain_pair", st, 2.0 * sizeof(T) * (double)g.total);
+    ProfScope ps(rows ? "plain_pair_planes" : "plain_pair_bundles", st, 2.0 * sizeof(T) * (double)g.total);
     if (rows) {
         const int64_t planes = g.total / M;
         const int64_t blocks = (planes + Q - 1) / Q;
@@ -790,6 +882,11 @@ int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed, bool pairs)
     const bool native = !(kFixable && fixed);
     for (int k = 0; k < g.d; ++k) {
         if (g.l[k] == 0) continue;
+        if (pairs && native && pair_square_fits<T>(g, k)) {
+            if (int e = launch_pair_square_any<T, OP>(u, g, k, st)) return e;
+            ++k;
+            continue;
+        }
         if (pairs && native) {
             if (const int Q = pair_tile<T>(g, k)) {
                 if (int e = launch_pair<T, OP>(u, g, k, Q, st)) return e;

@@ -32,11 +32,12 @@ SHAPES = [
     ((5, 5, 5, 5), 2, 2),       # planes, then bundles over 1089 positions (ragged last bundle)
     ((1, 1, 1, 1, 1, 1), 3, 3), # bundles over 9 positions: the second holds one
     ((2, 6, 6), 1, 0),
-    ((4, 2, 6, 5, 1), 2, 2),    # fp32: (0,1), (2,3) over 85 positions, 4 alone; fp64: (0,1), 2 alone, (3,4)
+    ((4, 2, 6, 5, 1), 2, 2),    # (0,1); dimension 2 alone (its pair tile is too large); (3,4)
     ((7, 3, 3), 1, 1),          # level 7 alone, pair (1,2) over 129 positions
     ((0, 5, 5), 0, 0),          # a dimension of one point: nothing below the pair to bundle
     ((5, 0, 5), 0, 0),
     ((2, 3, 2, 3, 2, 3), 3, 3),
+    ((1, 1, 4, 4, 4, 4), 3, 3),   # more tiles than resident CTAs: CTAs take two or more in turn
 ]
 
 
@@ -114,4 +115,5 @@ def test_pair_launches(levels, p32, p64, dt):
         run(u, levels, "h", dt, variant=variant)
         names = _lib.profile_read()
         _lib.profile_enable(False)
-        assert names.get("plain_pair", (0,))[0] == want
+        got = sum(names.get(k, (0,))[0] for k in ("plain_pair_planes", "plain_pair_bundles", "plain_pair_square"))
+        assert got == want

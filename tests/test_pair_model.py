@@ -40,12 +40,24 @@ def pair_tile(levels, k, es, batch=1):
     return B if (B * M <= cap and B <= Sa) else 0
 
 
+def square_fits(levels, k, es):
+    """The square kernel's test: outer pair of equal levels in [1, 5] with at
+    least one run of 64 bytes of positions below it."""
+    Sa = int(np.prod([2 ** l + 1 for l in levels[:k]]))
+    return (k >= 1 and k + 1 < len(levels) and levels[k] == levels[k + 1] and 1 <= levels[k] <= 5
+            and Sa >= 64 // es)
+
+
 def passes(levels, es):
-    """The plain path's passes: ('pair', k, Q) or ('single', k)."""
+    """The plain path's passes: ('square', k), ('pair', k, Q) or ('single', k)."""
     out, k = [], 0
     while k < len(levels):
         if levels[k] == 0:
             k += 1
+            continue
+        if square_fits(levels, k, es):
+            out.append(("square", k))
+            k += 2
             continue
         Q = pair_tile(levels, k, es)
         if Q:
@@ -117,21 +129,21 @@ def ctas_bundles(levels, k, B, es, batch):
 
 
 SHAPES = [(6, 6), (3, 4), (5, 5, 5, 5), (1, 1, 1, 1, 1, 1), (2, 6, 6), (4, 2, 6, 5, 1), (7, 3, 3),
-          (0, 5, 5), (5, 0, 5), (2, 3, 2, 3, 2, 3)]
+          (0, 5, 5), (5, 0, 5), (2, 3, 2, 3, 2, 3), (1, 1, 4, 4, 4, 4)]
 
 
 def test_pass_plan_matches_gpu_test_table():
     """The pair counts the GPU launch test expects follow from this model."""
     import test_gpu_pair as tg
     for levels, p32, p64 in tg.SHAPES:
-        assert sum(p[0] == "pair" for p in passes(levels, 4)) == p32, levels
-        assert sum(p[0] == "pair" for p in passes(levels, 8)) == p64, levels
+        assert sum(p[0] != "single" for p in passes(levels, 4)) == p32, levels
+        assert sum(p[0] != "single" for p in passes(levels, 8)) == p64, levels
 
 
 def test_headline_fp32_plan():
-    """(6,6,5,5,5) in fp32: planes of 65 x 65 (six per CTA), bundles of 16
-    positions for dimensions (2, 3), dimension 4 alone: three passes."""
-    assert passes((6, 6, 5, 5, 5), 4) == [("pair", 0, 6), ("pair", 2, 16), ("single", 4)]
+    """(6,6,5,5,5) in fp32: planes of 65 x 65 (six per CTA), the square
+    kernel for dimensions (2, 3), dimension 4 alone: three passes."""
+    assert passes((6, 6, 5, 5, 5), 4) == [("pair", 0, 6), ("square", 2), ("single", 4)]
 
 
 @pytest.mark.parametrize("levels", SHAPES + [(6, 6, 5, 5, 5)[:2] + (2, 2)])
@@ -144,6 +156,9 @@ def test_index_maps(levels, es, batch, misalign):
     total = batch * N
     shape = (batch,) + tuple(2 ** l + 1 for l in reversed(levels))
     for p in passes(levels, es):
+        if p[0] == "square":
+            check_square_maps(levels, p[1], es, batch, shape, total)
+            continue
         if p[0] != "pair":
             continue
         _, k, Q = p
@@ -179,6 +194,65 @@ def test_index_maps(levels, es, batch, misalign):
         assert (cover == 1).all()
 
 
+def ctas_square(levels, k, es, batch):
+    """Per CTA of the square kernel: for phase a the (grid index, shared
+    index) of every thread's pole, one row per thread, and for phase b the
+    (shared index, grid index) rows."""
+    n = 2 ** levels[k] + 1
+    B = 64 // es
+    Sa = int(np.prod([2 ** l + 1 for l in levels[:k]]))
+    total = batch * int(np.prod([2 ** l + 1 for l in levels]))
+    bpo = (Sa + B - 1) // B
+    blocks = total // (Sa * n * n) * bpo
+    tid = np.arange(B * n)
+    jj, q = tid & (B - 1), tid // B
+    i = np.arange(n)[None, :]
+    for blk in range(blocks):
+        o, jb = divmod(blk, bpo)
+        j0 = jb * B
+        act = j0 + jj < Sa
+        g = o * Sa * n * n + j0 + jj[act][:, None]
+        qa, ja = q[act][:, None], jj[act][:, None]
+        a_glob = g + Sa * n * qa + Sa * i
+        a_sm = (qa * n + i) * B + ja
+        b_sm = (i * n + qa) * B + ja
+        b_glob = g + Sa * qa + Sa * n * i
+        yield (a_glob, a_sm), (b_sm, b_glob), B * n * n
+
+
+def check_square_maps(levels, k, es, batch, shape, total):
+    rd = np.zeros(total, dtype=np.int64)
+    wr = np.zeros(total, dtype=np.int64)
+    for (a_glob, a_sm), (b_sm, b_glob), smem in ctas_square(levels, k, es, batch):
+        assert (a_glob >= 0).all() and (a_glob < total).all() and (b_glob >= 0).all() and (b_glob < total).all()
+        assert (a_sm >= 0).all() and (a_sm < smem).all() and (b_sm >= 0).all() and (b_sm < smem).all()
+        np.add.at(rd, a_glob.ravel(), 1)
+        np.add.at(wr, b_glob.ravel(), 1)
+        # phase b reads every shared slot phase a wrote, for the same grid point
+        s2g = np.full(smem, -1, dtype=np.int64)
+        s2g[a_sm.ravel()] = a_glob.ravel()
+        assert (s2g[b_sm] == b_glob).all()
+        for rows, dim in ((a_glob, k), (b_glob, k + 1)):
+            co = np.stack(np.unravel_index(rows, shape))
+            axis = len(levels) - dim
+            want = np.zeros(len(shape), dtype=np.int64)
+            want[axis] = 1
+            assert (np.diff(co, axis=2) == want[:, None, None]).all()
+            assert (co[axis, :, 0] == 0).all() and rows.shape[1] == shape[axis]
+    assert (rd == 1).all() and (wr == 1).all()
+
+
+def apply_square_model(u, levels, k, es, op1d):
+    out = u.copy()
+    for (a_glob, a_sm), (b_sm, b_glob), smem in ctas_square(levels, k, es, 1):
+        sm = np.full(smem, np.nan)
+        for gr, sr in zip(a_glob, a_sm):
+            sm[sr] = op1d(out[gr].copy(), levels[k])
+        for sr, gr in zip(b_sm, b_glob):
+            out[gr] = op1d(sm[sr].copy(), levels[k + 1])
+    return out
+
+
 def apply_pass_model(u, levels, k, Q, es, op1d):
     """One pair pass replayed through the modelled maps: each CTA's tile
     gathered, its poles swept with the 1-D transform, the tile stored."""
@@ -197,7 +271,7 @@ def apply_pass_model(u, levels, k, Q, es, op1d):
     return out
 
 
-@pytest.mark.parametrize("levels", [(3, 4), (2, 2, 3, 1), (4, 2, 3, 2, 1), (1, 3, 3, 2)])
+@pytest.mark.parametrize("levels", [(3, 4), (2, 2, 3, 1), (4, 2, 3, 2, 1), (1, 3, 3, 2), (2, 1, 3, 3), (3, 2, 2, 2, 2)])
 @pytest.mark.parametrize("op", ["h", "d"])
 def test_pass_model_reproduces_oracle(levels, op):
     op1d = {"h": lambda v, l: oracle.hierarchize(v, (l,)), "d": lambda v, l: oracle.dehierarchize(v, (l,))}[op]
@@ -207,7 +281,9 @@ def test_pass_model_reproduces_oracle(levels, op):
     N = u.size
     shape = tuple(2 ** l + 1 for l in reversed(levels))
     for p in passes(levels, 8):
-        if p[0] == "pair":
+        if p[0] == "square":
+            out = apply_square_model(out, levels, p[1], 8, op1d)
+        elif p[0] == "pair":
             out = apply_pass_model(out, levels, p[1], p[2], 8, op1d)
         else:
             k = p[1]
