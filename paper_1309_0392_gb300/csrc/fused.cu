@@ -1499,6 +1499,44 @@ int launch_lattice(const Plan &pl, const ClassPlan &cp, int k, const Geom &g, ST
 // Kernel variants of a plan (gbh_options.variant): 0 the interior-class
 // kernel of interior3.cu where it takes the tile, 1 the generic tile kernels
 // only.
+// Side streams of the one-lattice-dimension classes.  Classes of equal size
+// are independent: a class-C surplus reads only points of classes that
+// contain C (all of them larger, or C itself) and writes only class-C
+// points.  The classes of size 1 of a 3-D tile therefore run concurrently:
+// the first on the caller's stream, the others on two side streams that
+// fork from it and join it again by events (the dimension-0 lattice class,
+// latency bound on isolated 8-byte values, then overlaps the other two).
+// Created on the first fused call on a device; the enqueue sequence holds a
+// mutex so that concurrent host threads cannot interleave their event
+// records.
+struct SideStreams {
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    bool ok = false;
+};
+std::mutex g_side_mu;
+SideStreams g_side[64];
+
+// with g_side_mu held
+SideStreams *side_streams()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    SideStreams &ss = g_side[dev];
+    if (!ss.ok) {
+        bool good = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 2 && good; ++i)
+            good = cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!good) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ss.ok = true;
+    }
+    return &ss;
+}
+
 template <typename ST, bool FIX, int OP>
 int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st, bool int3)
 {
@@ -1507,7 +1545,24 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st, bool int3)
         if (c > 1) return launch_closure<ST, FIX, OP>(pl, pl.by_size[c], g, u, st);
         // classes with a compile-time kernel go one by one, the rest together
         std::vector<ClassPlan> rest;
-        for (const ClassPlan &cp : pl.by_size[c]) {
+        // size-1 classes with compile-time kernels: the second and third on
+        // the side streams
+        std::unique_lock<std::mutex> lk(g_side_mu, std::defer_lock);
+        SideStreams *ss = nullptr;
+        int nside = 0;
+        if (c == 1 && d == 3 && pl.by_size[1].size() > 1) {
+            lk.lock();
+            ss = side_streams();
+            if (ss && cudaEventRecord(ss->fork, st) != cudaSuccess) return check_launch();
+        }
+        // with side streams the classes are enqueued last to first: the later
+        // classes (one-lattice classes of dimensions 1 and 2, large closures)
+        // then take their SM slots first and the dimension-0 lattice class
+        // (small closures) fills the room beside them
+        const int ncls = (int)pl.by_size[c].size();
+        for (int idx = 0; idx < ncls; ++idx) {
+            const int pos = ss ? ncls - 1 - idx : idx;
+            const ClassPlan &cp = pl.by_size[c][pos];
             if (int3 && cp.mask == 0u) {
                 const int r = interior3_transform(reinterpret_cast<double *>(u), g, pl.m, OP, st);
                 if (r != 1) {
@@ -1515,10 +1570,22 @@ int run_plan(const Plan &pl, const Geom &g, ST *u, cudaStream_t st, bool int3)
                     continue;
                 }
             }
-            const int r = launch_tile3<ST, FIX, OP>(pl, cp, g, u, st);
+            cudaStream_t cs = st;
+            if (ss && pos > 0 && nside < 2) {
+                cs = ss->s[nside];
+                if (cudaStreamWaitEvent(cs, ss->fork, 0) != cudaSuccess) return check_launch();
+            }
+            const int r = launch_tile3<ST, FIX, OP>(pl, cp, g, u, cs);
             if (r == 1) rest.push_back(cp);
             else if (r != GBH_OK) return r;
+            if (cs != st) {
+                if (cudaEventRecord(ss->join[nside], cs) != cudaSuccess ||
+                    cudaStreamWaitEvent(st, ss->join[nside], 0) != cudaSuccess)
+                    return check_launch();
+                ++nside;
+            }
         }
+        if (lk.owns_lock()) lk.unlock();
         return launch_closure<ST, FIX, OP>(pl, rest, g, u, st);
     };
     if (OP == OP_H) {
