@@ -1026,6 +1026,8 @@ __device__ __forceinline__ float g_ld32(const float *p)
 constexpr int kGatherPer = 2;                      // points per thread
 constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
 constexpr int kGatherAhead = 4;                    // grids whose loads are in flight together
+constexpr int kGatherSmall = 64;                   // chunks up to this many points stage their terms
+constexpr int kGatherStage = 4096;                 // staged values per sub-batch (32 KB, dynamic)
 
 // A CTA takes a chunk of one subspace block (positions p, dimension 0
 // fastest) and runs through the grids containing the subspace in enumeration
@@ -1034,9 +1036,15 @@ constexpr int kGatherAhead = 4;                    // grids whose loads are in f
 // T_gk = S_k 2^{l_k - j_k + 1} (j_k >= 1) or S_k 2^{l_k} (j_k = 0, the two
 // boundary points).  Every term is one fused multiply-add, in grid order;
 // the loads of the next kGatherAhead grids are in flight while the current
-// ones are summed.
+// ones are summed.  A chunk of at most kGatherSmall points (the coarse
+// subspaces, whose grid lists are the longest) would leave most threads idle
+// and each point's thread with a long chain of dependent loads; there all
+// threads load the terms of up to kGatherStage / points grids at once into
+// shared memory, and each point's thread then runs its fused multiply-adds
+// over them in the same grid order.
 __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
 {
+    extern __shared__ double sV[];   // kGatherStage staged values (small chunks)
     __shared__ int64_t sB[256];
     __shared__ int64_t sT[256][kPlanMaxD];
     __shared__ double sC[256];
@@ -1073,6 +1081,21 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
                           : (double)g_ld32(reinterpret_cast<const float *>(sP[b]) + f);
         };
         const int q0 = P.list_off[sb], q1 = P.list_off[sb + 1];
+        const int64_t left = size - ch.y;
+        const int ppts = left < kGatherChunk ? (int)left : kGatherChunk;   // points of the chunk
+        const bool small = ppts <= kGatherSmall;
+        // value of the chunk's point pt in batch grid b
+        auto fetch_pt = [&](int b, int pt) -> double {
+            int64_t f = sB[b], rest = (int64_t)ch.y + pt;
+#pragma unroll
+            for (int k = 0; k < kPlanMaxD; ++k)
+                if (k < d) {
+                    f += (rest & ((1ll << sbits[k]) - 1)) * sT[b][k];
+                    rest >>= sbits[k];
+                }
+            return P.fp64 ? g_ld64(reinterpret_cast<const double *>(sP[b]) + f)
+                          : (double)g_ld32(reinterpret_cast<const float *>(sP[b]) + f);
+        };
         for (int qb = q0; qb < q1; qb += 256) {
             const int nb = q1 - qb < 256 ? q1 - qb : 256;
             if (tid < nb) {
@@ -1093,7 +1116,20 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
                 sP[tid] = P.ptrs[g];
             }
             __syncthreads();
-            if (npts > 0) {
+            if (small) {
+                const int GB = kGatherStage / ppts;             // grids per sub-batch (>= 64)
+                for (int b0 = 0; b0 < nb; b0 += GB) {
+                    const int cnt = (nb - b0 < GB ? nb - b0 : GB) * ppts;
+                    for (int w = tid; w < cnt; w += 256) {
+                        const int b = w / ppts;
+                        sV[w] = fetch_pt(b0 + b, w - b * ppts);
+                    }
+                    __syncthreads();
+                    if (tid < ppts)
+                        for (int w = tid, b = b0; w < cnt; w += ppts, ++b) acc[0] = __fma_rn(sC[b], sV[w], acc[0]);
+                    __syncthreads();
+                }
+            } else if (npts > 0) {
                 double cur[kGatherAhead][kGatherPer];
 #pragma unroll
                 for (int a = 0; a < kGatherAhead; ++a)
@@ -1758,6 +1794,16 @@ int build_sparse(gbh_plan *p)
             if (q > INT32_MAX) return GBH_ERANGE;
             chunks.push_back(make_int2(sb, (int)q));
         }
+    // costliest chunks first (points x grids containing the subspace), so
+    // that the long grid lists of the coarse subspaces do not finish last;
+    // each sparse point is still summed by one thread in grid order
+    {
+        auto cost = [&](const int2 &c) {
+            const int64_t pts = std::min<int64_t>(kGatherChunk, off[c.x + 1] - off[c.x] - c.y);
+            return pts * (int64_t)(loff[c.x + 1] - loff[c.x]);
+        };
+        std::stable_sort(chunks.begin(), chunks.end(), [&](const int2 &a, const int2 &b) { return cost(a) > cost(b); });
+    }
     p->nchunks = (int)chunks.size();
     if (int e = upload(&p->d_chunks, chunks)) return e;
     if (int e = upload(&p->d_sub_off, off)) return e;
@@ -2035,7 +2081,12 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
     G.fp64 = plan->dtype == GBH_F64;
     const int grid = std::max(1, std::min(G.nchunks, num_sms() * 4));
     ProfScope ps("gather", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * plan->sparse_points);
-    k_gather<<<grid, 256, 0, s>>>(G);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kGatherStage * sizeof(double)));
+        attr = true;
+    }
+    k_gather<<<grid, 256, kGatherStage * sizeof(double), s>>>(G);
     ps.done();
     count_launches(1);
     return check_launch();

@@ -95,9 +95,12 @@ def test_batched_arbitrary_levels_with_zero_levels():
         assert rel_err(g.cpu().numpy(), oracle.hierarchize(u, l), u, "h") <= TOL64
 
 
-@pytest.mark.parametrize("d,n", [(2, 5), (3, 4), (4, 4), (2, 9)])
+@pytest.mark.parametrize("d,n", [(2, 5), (3, 4), (4, 4), (2, 9), (4, 10)])
 def test_gather_bit_exact_on_oracle_surpluses(d, n):
-    """Same surpluses in, same summation order: the fp64 gather is bit-exact."""
+    """Same surpluses in, same summation order: the fp64 gather is bit-exact.
+    (4, 10): 589 grids, so the coarse subspaces' grid lists run over several
+    batches of 256 grids and several staged sub-batches of their small
+    chunks."""
     plan = gbh.Plan.scheme(d, n)
     lv, c = oracle.scheme(d, n)
     alphas = [oracle.hierarchize(inputs.scheme_grid(l, 1000 + g), l) for g, l in enumerate(lv)]
