@@ -1026,7 +1026,7 @@ __device__ __forceinline__ float g_ld32(const float *p)
 constexpr int kGatherPer = 2;                      // points per thread
 constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
 constexpr int kGatherAhead = 4;                    // grids whose loads are in flight together
-constexpr int kGatherSmall = 64;                   // chunks up to this many points stage their terms
+constexpr int kGatherSmall = 128;                  // chunks up to this many points stage their terms
 constexpr int kGatherStage = 4096;                 // staged values per sub-batch (32 KB, dynamic)
 
 // A CTA takes a chunk of one subspace block (positions p, dimension 0
