@@ -1026,8 +1026,12 @@ __device__ __forceinline__ float g_ld32(const float *p)
 constexpr int kGatherPer = 2;                      // points per thread
 constexpr int kGatherChunk = kGatherPer * 256;     // points per CTA chunk
 constexpr int kGatherAhead = 4;                    // grids whose loads are in flight together
-constexpr int kGatherSmall = 128;                  // chunks up to this many points stage their terms
-constexpr int kGatherStage = 4096;                 // staged values per sub-batch (32 KB, dynamic)
+// staged path per element type (measured): fp64 grids stage chunks of up to
+// 256 points, 8192 values per sub-batch (64 KB), three CTAs per SM; fp32
+// grids chunks of up to 128 points, 4096 values (32 KB), four CTAs per SM
+template <bool F64> struct GatherCfg {
+    static constexpr int small = F64 ? 256 : 128, stage = F64 ? 8192 : 4096, ctas = F64 ? 3 : 4;
+};
 
 // A CTA takes a chunk of one subspace block (positions p, dimension 0
 // fastest) and runs through the grids containing the subspace in enumeration
@@ -1036,15 +1040,16 @@ constexpr int kGatherStage = 4096;                 // staged values per sub-batc
 // T_gk = S_k 2^{l_k - j_k + 1} (j_k >= 1) or S_k 2^{l_k} (j_k = 0, the two
 // boundary points).  Every term is one fused multiply-add, in grid order;
 // the loads of the next kGatherAhead grids are in flight while the current
-// ones are summed.  A chunk of at most kGatherSmall points (the coarse
+// ones are summed.  A chunk of at most GatherCfg::small points (the coarse
 // subspaces, whose grid lists are the longest) would leave most threads idle
 // and each point's thread with a long chain of dependent loads; there all
-// threads load the terms of up to kGatherStage / points grids at once into
+// threads load the terms of up to GatherCfg::stage / points grids at once into
 // shared memory, and each point's thread then runs its fused multiply-adds
 // over them in the same grid order.
-__global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
+template <bool F64>
+__global__ void __launch_bounds__(256, GatherCfg<F64>::ctas) k_gather(const GatherParams P)
 {
-    extern __shared__ double sV[];   // kGatherStage staged values (small chunks)
+    extern __shared__ double sV[];   // GatherCfg::stage staged values (small chunks)
     __shared__ int64_t sB[256];
     __shared__ int64_t sT[256][kPlanMaxD];
     __shared__ double sC[256];
@@ -1083,7 +1088,7 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
         const int q0 = P.list_off[sb], q1 = P.list_off[sb + 1];
         const int64_t left = size - ch.y;
         const int ppts = left < kGatherChunk ? (int)left : kGatherChunk;   // points of the chunk
-        const bool small = ppts <= kGatherSmall;
+        const bool small = ppts <= GatherCfg<F64>::small;
         // value of the chunk's point pt in batch grid b
         auto fetch_pt = [&](int b, int pt) -> double {
             int64_t f = sB[b], rest = (int64_t)ch.y + pt;
@@ -1117,7 +1122,7 @@ __global__ void __launch_bounds__(256, 4) k_gather(const GatherParams P)
             }
             __syncthreads();
             if (small) {
-                const int GB = kGatherStage / ppts;             // grids per sub-batch (>= 64)
+                const int GB = GatherCfg<F64>::stage / ppts;    // grids per sub-batch (>= 16)
                 for (int b0 = 0; b0 < nb; b0 += GB) {
                     const int cnt = (nb - b0 < GB ? nb - b0 : GB) * ppts;
                     for (int w = tid; w < cnt; w += 256) {
@@ -2083,10 +2088,12 @@ int gbh_plan_gather(gbh_plan *plan, double *sparse, void *stream)
     ProfScope ps("gather", s, (double)plan->total_points * (plan->dtype == GBH_F64 ? 8 : 4) + 8.0 * plan->sparse_points);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kGatherStage * sizeof(double)));
+        cudaFuncSetAttribute(k_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GatherCfg<true>::stage * sizeof(double)));
+        cudaFuncSetAttribute(k_gather<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(GatherCfg<false>::stage * sizeof(double)));
         attr = true;
     }
-    k_gather<<<grid, 256, kGatherStage * sizeof(double), s>>>(G);
+    if (G.fp64) k_gather<true><<<grid, 256, GatherCfg<true>::stage * sizeof(double), s>>>(G);
+    else k_gather<false><<<grid, 256, GatherCfg<false>::stage * sizeof(double), s>>>(G);
     ps.done();
     count_launches(1);
     return check_launch();
