@@ -168,9 +168,9 @@ constexpr int kGroupLevel = 12;                  // block level of long dimensio
 constexpr int kGroupElems = 8208;               // shared-memory elements per item
 // fused kernel: tile size (elements), CTAs per SM, and the block level of
 // dimensions longer than a tile
-constexpr int kFusedElems = 6144;
-constexpr int kFusedCtas64 = 4;                  // resident CTAs per SM, fp64 / fp32 plans
-constexpr int kFusedCtas32 = 6;
+constexpr int kFusedElems = 8192;
+constexpr int kFusedCtas64 = 3;                  // resident CTAs per SM, fp64 / fp32 plans
+constexpr int kFusedCtas32 = 5;
 constexpr int kGroupedCtas = 3;                  // single-grid grouped launches
 constexpr int kSplitLevel = 12;
 
