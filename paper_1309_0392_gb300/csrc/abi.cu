@@ -198,7 +198,8 @@ int gbh_transform_batched(void *data, int64_t batch, int d, const int32_t *level
     if (tp != GBH_PATH_PLAIN && g.N >= 4096 && fused_preferred(g, dtype, op))
         return fused_transform(data, g, dtype, op, opt, s);
     // fp64 sweeps compute in fixed point unless native arithmetic is asked for
-    return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1), pairs);
+    // the default arithmetic (arith = 0) lets dimensions of level 1 compute natively
+    return plain_transform(data, g, dtype, op, s, !(opt && opt->arith == 1), pairs, !(opt && opt->arith != 0));
 }
 
 int gbh_hierarchize(void *data, int d, const int32_t *levels, int dtype, void *stream)

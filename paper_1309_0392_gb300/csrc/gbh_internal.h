@@ -59,8 +59,10 @@ int grouped_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t
 // order, bit-identical to the serial algorithm).  pairs: with native
 // arithmetic, two consecutive dimensions per pass where their poles fit a
 // pair tile (same results, one memory crossing fewer per pair).
+// short_native: with fixed64, dimensions of level 1 compute natively (and may
+// pair); the default route asks for it, an explicit fixed-point request not.
 int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64 = false,
-                    bool pairs = true);
+                    bool pairs = true, bool short_native = false);
 
 // Fused path: dyadic tiles (class-ordered), see fused.cu.
 int fused_transform(void *data, const Geom &g, int dtype, int op, const gbh_options *opt,

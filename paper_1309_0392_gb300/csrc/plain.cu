@@ -572,8 +572,9 @@ k_pair(T *__restrict__ u, int64_t units, int64_t Sa, int64_t bpo, int la, int lb
 }
 
 // Square pairs of outer dimensions (a >= 1, l_a = l_b = L <= 5): no staging
-// copy.  A CTA owns B = 64 / sizeof(T) consecutive positions j (runs of 64
-// bytes) and n = 2^L + 1 threads per position.  Thread (jj, q) loads the pole
+// copy.  A CTA owns B consecutive positions j (square_run: runs of at least
+// 64 bytes, more positions for short poles) and n = 2^L + 1 threads per
+// position.  Thread (jj, q) loads the pole
 // of dimension a at i_{a+1} = q straight from global memory into registers
 // (a warp reads whole runs: coalesced), transforms it and parks it in shared
 // memory; after one barrier it takes the pole of dimension a+1 at i_a = q
@@ -582,17 +583,21 @@ k_pair(T *__restrict__ u, int64_t units, int64_t Sa, int64_t bpo, int la, int lb
 // one load per point), and every thread keeps a whole pole of loads in
 // flight.  Shared index (i_{a+1} n + i_a) B + jj: the two positions of q in
 // a warp fall on opposite bank halves in both phases.
-template <typename T>
+// positions per CTA: runs of at least 64 bytes, and for short poles as many
+// positions as keep the CTA near 256 threads (a power of two)
+template <typename T, int L>
 __host__ __device__ constexpr int square_run()
 {
-    return 64 / (int)sizeof(T);
+    constexpr int n = (1 << L) + 1, by_bytes = 64 / (int)sizeof(T);
+    constexpr int by_threads = 256 / n >= 64 ? 64 : 256 / n >= 32 ? 32 : 256 / n >= 16 ? 16 : 256 / n >= 8 ? 8 : 4;
+    return by_bytes > by_threads ? by_bytes : by_threads;
 }
 
 template <typename T, int OP, int L>
-__global__ void __launch_bounds__(square_run<T>() * ((1 << L) + 1), 2)
+__global__ void __launch_bounds__(square_run<T, L>() * ((1 << L) + 1), 2)
 k_pair_square(T *__restrict__ u, int64_t Sa, int64_t bpo)
 {
-    constexpr int n = (1 << L) + 1, B = square_run<T>();
+    constexpr int n = (1 << L) + 1, B = square_run<T, L>();
     extern __shared__ __align__(16) unsigned char smr[];
     T *sv = reinterpret_cast<T *>(smr);
     const int tid = threadIdx.x;
@@ -624,7 +629,7 @@ k_pair_square(T *__restrict__ u, int64_t Sa, int64_t bpo)
 template <typename T, int OP, int L>
 int launch_pair_square(T *u, const Geom &g, int k, cudaStream_t st)
 {
-    constexpr int n = (1 << L) + 1, B = square_run<T>();
+    constexpr int n = (1 << L) + 1, B = square_run<T, L>();
     const int64_t Sa = g.S[k];
     const int64_t bpo = (Sa + B - 1) / B;
     const int64_t blocks = g.total / (Sa * n * n) * bpo;
@@ -647,8 +652,16 @@ int launch_pair_square(T *u, const Geom &g, int k, cudaStream_t st)
 template <typename T>
 bool pair_square_fits(const Geom &g, int k)
 {
-    return k >= 1 && k + 1 < g.d && g.l[k] == g.l[k + 1] && g.l[k] >= 1 && g.l[k] <= 5 &&
-           g.S[k] >= square_run<T>();
+    if (!(k >= 1 && k + 1 < g.d && g.l[k] == g.l[k + 1] && g.l[k] >= 1 && g.l[k] <= 5)) return false;
+    int B = 0;
+    switch (g.l[k]) {
+        case 1: B = square_run<T, 1>(); break;
+        case 2: B = square_run<T, 2>(); break;
+        case 3: B = square_run<T, 3>(); break;
+        case 4: B = square_run<T, 4>(); break;
+        default: B = square_run<T, 5>(); break;
+    }
+    return g.S[k] >= B;
 }
 
 template <typename T, int OP>
@@ -874,49 +887,58 @@ int launch_pair(T *u, const Geom &g, int k, int Q, cudaStream_t st)
 }
 
 // pairs: two consecutive dimensions per pass where they fit a pair tile
-// (native arithmetic only)
+// (native arithmetic only).  short_native: with fixed point, dimensions of
+// level 1 still compute natively -- a 3-point pole costs two fp64 operations,
+// less than its fixed-point scale pass and conversions -- and so can pair.
+constexpr int kShortNativeLevel = 1;
+
 template <typename T, int OP>
-int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed, bool pairs)
+int plain_all(T *u, const Geom &g, cudaStream_t st, bool fixed, bool pairs, bool short_native)
 {
     constexpr bool kFixable = sizeof(T) == 8 && OP != OP_DT;
-    const bool native = !(kFixable && fixed);
+    auto native = [&](int k) {
+        return !(kFixable && fixed) || (short_native && g.l[k] <= kShortNativeLevel);
+    };
     for (int k = 0; k < g.d; ++k) {
         if (g.l[k] == 0) continue;
-        if (pairs && native && pair_square_fits<T>(g, k)) {
+        const bool nat = native(k), nat2 = nat && k + 1 < g.d && native(k + 1);
+        if (pairs && nat2 && pair_square_fits<T>(g, k)) {
             if (int e = launch_pair_square_any<T, OP>(u, g, k, st)) return e;
             ++k;
             continue;
         }
-        if (pairs && native) {
+        if (pairs && nat2) {
             if (const int Q = pair_tile<T>(g, k)) {
                 if (int e = launch_pair<T, OP>(u, g, k, Q, st)) return e;
                 ++k;
                 continue;
             }
         }
-        if (int e = sweep_dim<T, OP>(u, g, k, st, fixed)) return e;
+        if (int e = sweep_dim<T, OP>(u, g, k, st, fixed && !nat)) return e;
     }
     return GBH_OK;
 }
 
 template <typename T>
-int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed, bool pairs)
+int plain_dispatch(T *u, const Geom &g, int op, cudaStream_t st, bool fixed, bool pairs, bool short_native)
 {
     switch (op) {
-        case OP_H: return plain_all<T, OP_H>(u, g, st, fixed, pairs);
-        case OP_D: return plain_all<T, OP_D>(u, g, st, fixed, pairs);
-        case OP_A: return plain_all<T, OP_A>(u, g, st, fixed, pairs);
-        case OP_DT: return plain_all<T, OP_DT>(u, g, st, false, pairs);
+        case OP_H: return plain_all<T, OP_H>(u, g, st, fixed, pairs, short_native);
+        case OP_D: return plain_all<T, OP_D>(u, g, st, fixed, pairs, short_native);
+        case OP_A: return plain_all<T, OP_A>(u, g, st, fixed, pairs, short_native);
+        case OP_DT: return plain_all<T, OP_DT>(u, g, st, false, pairs, short_native);
         default: return GBH_EINVAL;
     }
 }
 
 }  // namespace
 
-int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64, bool pairs)
+int plain_transform(void *data, const Geom &g, int dtype, int op, cudaStream_t s, bool fixed64, bool pairs,
+                    bool short_native)
 {
-    if (dtype == GBH_F64) return plain_dispatch<double>(static_cast<double *>(data), g, op, s, fixed64, pairs);
-    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s, false, pairs);
+    if (dtype == GBH_F64)
+        return plain_dispatch<double>(static_cast<double *>(data), g, op, s, fixed64, pairs, short_native);
+    if (dtype == GBH_F32) return plain_dispatch<float>(static_cast<float *>(data), g, op, s, false, pairs, false);
     return GBH_EDTYPE;
 }
 

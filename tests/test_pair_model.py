@@ -40,12 +40,25 @@ def pair_tile(levels, k, es, batch=1):
     return B if (B * M <= cap and B <= Sa) else 0
 
 
+def square_run(es, L):
+    """Positions per CTA of the square kernel: runs of at least 64 bytes, and
+    for short poles as many positions as keep the CTA near 256 threads."""
+    n = 2 ** L + 1
+    by_threads = 4
+    for b in (64, 32, 16, 8):
+        if 256 // n >= b:
+            by_threads = b
+            break
+    return max(64 // es, by_threads)
+
+
 def square_fits(levels, k, es):
     """The square kernel's test: outer pair of equal levels in [1, 5] with at
-    least one run of 64 bytes of positions below it."""
+    least one run of positions below it."""
+    if not (k >= 1 and k + 1 < len(levels) and levels[k] == levels[k + 1] and 1 <= levels[k] <= 5):
+        return False
     Sa = int(np.prod([2 ** l + 1 for l in levels[:k]]))
-    return (k >= 1 and k + 1 < len(levels) and levels[k] == levels[k + 1] and 1 <= levels[k] <= 5
-            and Sa >= 64 // es)
+    return Sa >= square_run(es, levels[k])
 
 
 def passes(levels, es):
@@ -199,7 +212,7 @@ def ctas_square(levels, k, es, batch):
     index) of every thread's pole, one row per thread, and for phase b the
     (shared index, grid index) rows."""
     n = 2 ** levels[k] + 1
-    B = 64 // es
+    B = square_run(es, levels[k])
     Sa = int(np.prod([2 ** l + 1 for l in levels[:k]]))
     total = batch * int(np.prod([2 ** l + 1 for l in levels]))
     bpo = (Sa + B - 1) // B
