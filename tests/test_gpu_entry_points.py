@@ -1,8 +1,9 @@
 """The four single-grid entry points of the C ABI (gbh_hierarchize,
 gbh_dehierarchize, gbh_hierarchize_adjoint, gbh_dehierarchize_adjoint; the
 paper's problem statement, Sec. 3) called directly through ctypes with valid
-device data, and a CUDA graph that captures a plan's batched transform and its
-gather, replayed and compared with the oracle (Sec. 2)."""
+device data, a CUDA graph that captures a plan's batched transform and its
+gather, replayed and compared with the oracle (Sec. 2), and a graph that
+captures a single-grid fused hierarchization with its forked streams."""
 import ctypes
 
 import numpy as np
@@ -119,3 +120,30 @@ def test_graph_replay_of_batched_transform_and_gather(dtype):
             alphas.append(a)
         # the gather of the replay's own surpluses, bit for bit
         assert np.array_equal(sparse.cpu().numpy(), oracle.gather(d, n, lv, c, alphas)), replay
+
+
+def test_graph_replay_of_fused_single_grid_hierarchization():
+    """A 3-D fp64 grid on the fused path (tiles (5,4,4)) forks its
+    one-lattice-dimension classes onto side streams and joins them back by
+    events.  Captured in a CUDA graph, the fork and join become graph edges;
+    two replays on fresh data match the oracle."""
+    levels = (9, 8, 8)
+    st = torch.cuda.Stream()
+    t = torch.empty(inputs.num_points(levels), dtype=torch.float64, device="cuda")
+    # warm-up outside the capture (first calls create the side streams and
+    # set kernel attributes)
+    with torch.cuda.stream(st):
+        t.copy_(torch.from_numpy(inputs.uniform(levels, 61)))
+        gbh.hierarchize(t, levels)
+        gbh.dehierarchize(t, levels)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        gbh.hierarchize(t, levels)
+    for seed in (62, 63):
+        u = inputs.uniform(levels, seed)
+        t.copy_(torch.from_numpy(u))
+        torch.cuda.synchronize()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert rel_err(t.cpu().numpy(), oracle.hierarchize(u, levels), u, "h") <= TOL64
